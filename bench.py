@@ -1,0 +1,392 @@
+#!/usr/bin/env python3
+"""Benchmark: FastSV connected components on one GB300 (or N replicas).
+
+One step = one complete FastSV solve (set-up + every iteration until f[f]
+stops changing) of the workload through the C ABI.  Default workload: R-MAT
+scale 26, edge factor 16, ids permuted (67,108,864 vertices, ~2.1e9 directed
+CSR entries, int64 row_ptr).  The metric is directed CSR entries per second
+of the whole solve (GTEPS = 1e9 entries/s), inputs resident in HBM.
+
+Also reported:
+  e2e          the same metric through fastsv_cc_host from pinned host
+               buffers: the host-to-device copy of row_ptr/col_idx and the
+               copy back of the labels are inside every timed step;
+  roofline     the hooking kernel (k2_hook, the largest share of device
+               time): counted algorithmic bytes per launch / its average
+               duration (CUDA events on its stream, host-loop pass over the
+               same steps) against the measured HBM copy bandwidth;
+  cpu_baseline the CPU oracle (OpenMP Algorithm 2) on the same graph on the
+               host cores.
+
+--impl reference times the CPU oracle as the reference arm.
+Multi-GPU (torchrun): every rank solves its own replica of the workload
+(the single-graph solve does not shard); value = all ranks' entries / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import graphgen  # noqa: E402
+
+WORKLOADS = {
+    "rmat_s26_perm": dict(desc="R-MAT scale 26, edge factor 16, a/b/c=.57/.19/.19, ids permuted, seed 3",
+                          bits=64),
+    "rmat_s16": dict(desc="R-MAT scale 16, edge factor 16, seed 1", bits=32),
+    "grid_4096_p055_iso1M": dict(desc="4096x4096 lattice, p=0.55, +1M isolated, seed 2", bits=32),
+}
+METRIC = "CC |E|/s (GTEPS) + %HBM peak at R-MAT s26"
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def kernel_source_hash() -> str:
+    p = os.path.join(ROOT, "paper_1910_05971_gb300", "csrc", "fastsv_kernels.cuh")
+    with open(p, "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def profiled_traffic(workload: str):
+    """DRAM bytes per k2_hook launch from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "k2_hook_traffic.txt")
+    try:
+        rows = {}
+        with open(p) as fh:
+            for line in fh:
+                if "=" in line and not line.startswith("#"):
+                    k, v = line.split("=", 1)
+                    rows[k.strip()] = v.strip()
+        if rows.get("kernel_source_sha256_16") != kernel_source_hash() or rows.get("workload") != workload:
+            return None
+        return float(rows["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def make_graph(workload: str):
+    t0 = time.time()
+    rp, ci = graphgen.WORKLOADS[workload]()
+    log(f"[bench] generated {workload}: n={len(rp) - 1} m={len(ci)} in {time.time() - t0:.1f}s")
+    return rp, ci
+
+
+def cpu_oracle_time(rp, ci, max_seconds: float = 30.0):
+    """Time the CPU oracle (OpenMP Algorithm 2, all host threads) on the
+    graph.  The sample is the full solve when it fits the time bound; else a
+    prefix of iterations, scaled by the iterations the solve needs."""
+    import oracle
+    nthreads = os.cpu_count() or 1
+    t0 = time.time()
+    f, it1, conv1, _ = oracle.fastsv(rp, ci, form="omp", nthreads=nthreads, max_iters=1)
+    t_first = time.time() - t0
+    if conv1:
+        return dict(seconds=t_first, iterations=1, sample="full solve (1 iteration)", cores=nthreads)
+    if t_first * 8 <= max_seconds:
+        t0 = time.time()
+        f, it, conv, _ = oracle.fastsv(rp, ci, form="omp", nthreads=nthreads)
+        return dict(seconds=time.time() - t0, iterations=it, sample=f"full solve ({it} iterations)",
+                    cores=nthreads)
+    return dict(seconds=t_first, iterations=1, sample="first iteration only (time per iteration)",
+                cores=nthreads, per_iteration=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="fastsv", choices=["fastsv", "reference"])
+    ap.add_argument("--workload", default="rmat_s26_perm", choices=sorted(WORKLOADS))
+    ap.add_argument("--k2-items", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import paper_1910_05971_gb300 as fsv
+
+    assert torch.cuda.is_available(), "bench.py needs a CUDA device"
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    wl = WORKLOADS[args.workload]
+    bits = wl["bits"]
+    rp, ci = make_graph(args.workload)
+    n, m = len(rp) - 1, len(ci)
+    rp_dev = torch.from_numpy(rp.astype(np.int64 if bits == 64 else np.int32)).cuda()
+    ci_dev = torch.from_numpy(ci).cuda()
+    labels = torch.empty(n, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    solver = fsv.FastSV(rowptr_bits=bits, k2_items=args.k2_items)
+    for _ in range(args.warmup):
+        solver.cc(rp_dev, ci_dev, labels)
+    st = solver.stats()
+    iterations = st["iterations"]
+
+    # ---- timed region: K solves, inputs resident in HBM (9 GB >> 129 MB L2) ----
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    sampler = ClockSampler(local_rank)
+    launches0 = solver.kernel_launches()
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        solver.cc(rp_dev, ci_dev, labels, check_status=False)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    solver.check_last()
+    launches = solver.kernel_launches() - launches0
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * m / (ms * 1e-3) / 1e9
+
+    # ---- dominant kernel: k2_hook durations from CUDA events (host-loop pass) ----
+    prof = fsv.FastSV(rowptr_bits=bits, k2_items=args.k2_items, use_graph=False)
+    k2_ms, k3_ms, it_sum = 0.0, 0.0, 0
+    for _ in range(args.steps):
+        prof.cc(rp_dev, ci_dev, labels)
+        sp = prof.stats()
+        k2_ms += sp["ms_k2"]
+        k3_ms += sp["ms_k3"]
+        it_sum += sp["iterations"]
+    prof.close()
+    k2_avg_ms = k2_ms / it_sum
+    k3_avg_ms = k3_ms / it_sum
+    r = 8 if bits == 64 else 4
+    k2_bytes = r * (n + 1) + 8 * m + 24 * n          # counted model per hooking launch
+    k3_bytes = 20 * n
+    peaks, peak_src = measured_peaks()
+    peak = float(peaks["hbm_gbs"])
+    k2_gbs = k2_bytes / (k2_avg_ms * 1e-3) / 1e9
+    traffic = profiled_traffic(args.workload)
+
+    # ---- end to end through the host-buffer entry point ----
+    e2e = None
+    if not args.no_e2e:
+        rp_h = torch.from_numpy(rp.astype(np.int64 if bits == 64 else np.int32)).pin_memory()
+        ci_h = torch.from_numpy(ci).pin_memory()
+        lab_h = torch.empty(n, dtype=torch.int32).pin_memory()
+        hsolver = fsv.FastSV(rowptr_bits=bits, k2_items=args.k2_items)
+        hsolver.cc_host(rp_h, ci_h, lab_h)
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            hsolver.cc_host(rp_h, ci_h, lab_h)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        wall = (time.perf_counter() - t0) / args.steps
+        ms_e2e = max(e0.elapsed_time(e1) / args.steps, wall * 1e3)
+        if dist is not None:
+            t = torch.tensor([ms_e2e], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_e2e = float(t.item())
+        hsolver.close()
+        ok = bool(torch.equal(lab_h, labels.cpu()))
+        e2e = {"value": world * m / (ms_e2e * 1e-3) / 1e9, "unit": "GTEPS",
+               "h2d_bytes_per_step": int(rp_h.numel() * rp_h.element_size() + ci_h.numel() * 4),
+               "d2h_bytes_per_step": int(n * 4), "ms_per_step": ms_e2e, "labels_match_device_path": ok}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        c = cpu_oracle_time(rp, ci)
+        if c.get("per_iteration"):
+            secs = c["seconds"] * iterations
+            sample = c["sample"] + f", scaled by the {iterations} iterations of the solve"
+        else:
+            secs = c["seconds"]
+            sample = c["sample"]
+        cpu = {"value": m / secs / 1e9, "unit": "GTEPS", "cores": c["cores"], "kind": "oracle",
+               "sample": f"{args.workload}: {sample}, OpenMP Algorithm 2 on the host cores",
+               "seconds": secs}
+
+    solver.close()
+    if rank == 0:
+        out = {
+            "metric": METRIC,
+            "value": value,
+            "unit": "GTEPS",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": ms,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "desc": wl["desc"], "n": n, "m_directed": m,
+                       "m_undirected": m // 2, "rowptr_bits": bits, "iterations": iterations,
+                       "parallelism": f"replicas{world}" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (col_idx alone is 4m bytes), no flush",
+                       "k2_items": args.k2_items},
+            "roofline": {"bound": "hbm", "achieved": k2_gbs, "peak": peak, "unit": "GB/s",
+                         "frac": k2_gbs / peak, "traffic": traffic,
+                         "kernel": "k2_hook", "algorithmic_bytes_per_launch": k2_bytes,
+                         "avg_launch_ms": k2_avg_ms, "peak_source": f"{peak_src} hbm_gbs",
+                         "k3_grandparent": {"algorithmic_bytes_per_launch": k3_bytes, "avg_launch_ms": k3_avg_ms,
+                                            "achieved": k3_bytes / (k3_avg_ms * 1e-3) / 1e9}},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+        }
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the CPU oracle (OpenMP Algorithm 2) on the host cores,
+    same workload, metric and unit; rank 0 only."""
+    if rank != 0:
+        return
+    import oracle
+    rp, ci = make_graph(args.workload)
+    n, m = len(rp) - 1, len(ci)
+    nthreads = os.cpu_count() or 1
+    f, it, conv, _ = oracle.fastsv(rp, ci, form="omp", nthreads=nthreads, max_iters=1)
+    t0 = time.time()
+    oracle.fastsv(rp, ci, form="omp", nthreads=nthreads, max_iters=1)
+    t_iter = time.time() - t0
+    full = t_iter * 6 <= 20.0
+    # the iteration count of the whole solve (oracle's own)
+    if full:
+        f, iters, conv, _ = oracle.fastsv(rp, ci, form="omp", nthreads=nthreads)
+    else:
+        iters = None
+    for _ in range(max(0, args.warmup - 1)):
+        if full:
+            oracle.fastsv(rp, ci, form="omp", nthreads=nthreads)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.time()
+        if full:
+            oracle.fastsv(rp, ci, form="omp", nthreads=nthreads)
+        else:
+            oracle.fastsv(rp, ci, form="omp", nthreads=nthreads, max_iters=1)
+        times.append(time.time() - t0)
+    step = float(np.mean(times))
+    if not full:
+        f, iters, conv, _ = oracle.fastsv(rp, ci, form="omp", nthreads=nthreads)
+        step = step * iters
+        sample = f"first iteration per step, scaled by the oracle's {iters} iterations"
+    else:
+        sample = f"full solve per step ({iters} iterations)"
+    value = m / step / 1e9
+    out = {"metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": step * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "int32", "data": "synthetic", "impl": "reference",
+           "config": {"workload": args.workload, "n": n, "m_directed": m, "iterations": iters},
+           "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": nthreads, "kind": "oracle",
+                            "sample": f"{args.workload}: {sample}"},
+           "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,224 @@
+/*
+ * fastsv.h -- C ABI of libfastsv, FastSV connected components on one GB300 GPU.
+ *
+ * Method: Y. Zhang, A. Azad, Z. Hu, "FastSV: A Distributed-Memory Connected
+ * Component Algorithm with Fast Convergence" (arXiv:1910.05971).
+ *
+ * Every solve runs Algorithm 2 (Section 3) on the device:
+ *   repeat
+ *     mngf[u]      = min_{v in N(u)} gf[v]          ((select2nd,min) SpMV, Section 4.1)
+ *     f_next[f[u]] <-min mngf[u]                    stochastic hooking (Section 3.2)
+ *     f_next[u]    <-min mngf[u]                    aggressive hooking (Section 3.3)
+ *     f_next[u]    <-min gf[u]                      shortcutting
+ *     f <- f_next;  gf <- f[f]
+ *   until gf is unchanged                            early termination (Section 3.4)
+ * and returns labels[u] = f[u] = the smallest vertex id in u's connected
+ * component (the converged state of Section 3.4, proved in Appendix A).
+ * All arithmetic is int32 compare/min; results are exact and deterministic.
+ *
+ * Conventions for every entry point:
+ *  - Graphs are undirected and given in CSR form with each edge {u,v} stored
+ *    in both rows (symmetric).  Self-loops and duplicate entries are allowed
+ *    and change neither the labels nor the iteration sequence.  Rows need not
+ *    be sorted.  Vertex ids are int32 in [0, n).
+ *  - "device" pointers must point to memory of the current CUDA device;
+ *    "host" pointers to host memory (pinned memory gives full copy speed).
+ *    All arrays are owned by the caller; the library never frees them and
+ *    keeps no reference after the call's work has completed on the stream.
+ *  - The handle owns its device workspace (snapshot and grandparent vectors,
+ *    tile lists, counters) and grows it on demand; it is freed by
+ *    fastsv_destroy.  A handle is not thread-safe: use one per host thread.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Work is enqueued on it; calls return after enqueueing, except
+ *    where a call says it synchronises.
+ *  - Argument errors detectable on the host return at once with
+ *    FASTSV_ERR_INVALID_ARG and enqueue nothing.  Errors found on the device
+ *    (iteration cap, invalid CSR when validation is on) are reported by
+ *    fastsv_get_stats.
+ */
+#ifndef FASTSV_H
+#define FASTSV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fastsv_ctx* fastsv_t;
+
+typedef enum {
+    FASTSV_OK = 0,
+    FASTSV_ERR_INVALID_ARG = 1,   /* bad pointer, size or option; nothing was enqueued */
+    FASTSV_ERR_OOM = 2,           /* device or pinned allocation failed; the handle stays usable */
+    FASTSV_ERR_CUDA = 3,          /* a CUDA runtime call failed; see fastsv_last_cuda_error */
+    FASTSV_ERR_MAX_ITERS = 4,     /* the iteration cap was reached before f[f] stopped changing */
+    FASTSV_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up */
+    FASTSV_ERR_UNSUPPORTED = 6,   /* option or size this build does not handle */
+    FASTSV_ERR_INVALID_GRAPH = 7, /* validation found a malformed CSR (bounds, monotonicity, symmetry) */
+    FASTSV_ERR_FULL = 8           /* pool: no slot or not enough budget for the request right now */
+} fastsv_status;
+
+/* Solver variants.  FASTSV_MODE_SYNC is Algorithm 2 exactly: every update of
+ * an iteration reads the vectors as they were at its start (the f / f_next
+ * separation of Section 2.4), so the pointer graph after iteration i is the
+ * same on every run and equal to the CPU oracle's.  FASTSV_MODE_ASYNC reads
+ * and writes one vector in place (the concurrent variant Section 2.4
+ * mentions): labels are the same, iteration counts may differ. */
+enum { FASTSV_MODE_SYNC = 0, FASTSV_MODE_ASYNC = 1 };
+
+typedef struct {
+    int32_t rowptr_bits;   /* width of row_ptr entries in fastsv_cc / fastsv_cc_host: 32 or 64 (default 64) */
+    int32_t mode;          /* FASTSV_MODE_SYNC (default) or FASTSV_MODE_ASYNC */
+    int32_t max_iters;     /* iteration cap per graph (default 4096); reaching it gives FASTSV_ERR_MAX_ITERS */
+    int32_t validate;      /* 0 off (default); 1 check row_ptr monotonicity and neighbour ids in [0,n);
+                              2 also check symmetry (rows must then be sorted).  Validation synchronises. */
+    int32_t use_graph;     /* 1 (default): the iteration loop runs on the device inside a CUDA graph
+                              conditional WHILE node, with no host synchronisation per iteration;
+                              0: host loop, one synchronisation per iteration, per-kernel timings */
+    int32_t k2_items;      /* merge-path items per thread in the hooking kernel (0 = default) */
+    int32_t grid_ctas_per_sm; /* persistent CTAs per SM for the iteration kernels (0 = occupancy limit) */
+    int32_t l2_persist;    /* 1: mark the gathered grandparent vector as persisting in L2 (default 0) */
+    int32_t timing;        /* 1: record device time of each call with CUDA events (default 1) */
+    int32_t fail_alloc_after; /* test hook: >0 makes the N-th workspace allocation of this handle fail
+                                 (returns FASTSV_ERR_OOM); 0 off */
+    int32_t reserved[6];
+} fastsv_options;
+
+typedef struct {
+    int64_t n;                 /* vertices of the last call (sum over graphs for batched calls) */
+    int64_t m;                 /* directed CSR entries of the last call */
+    int64_t iterations;        /* iterations executed (single-graph calls; max over graphs for batched) */
+    int32_t status;            /* fastsv_status of the last call, including device-detected errors */
+    int32_t converged;         /* 1 if every graph reached an unchanged f[f] */
+    float ms_total;            /* device time of the last call's work on its stream (timing = 1) */
+    float ms_setup;            /* of which: partitioning, state initialisation, validation */
+    float ms_k2;               /* host-loop mode only: total time of the hooking kernel */
+    float ms_k3;               /* host-loop mode only: total time of the grandparent kernel */
+    int32_t trace_len;         /* entries valid in changed_per_iter */
+    int32_t reserved;
+    int64_t changed_per_iter[64]; /* single-graph calls: grandparents changed in iteration i */
+} fastsv_stats;
+
+/* Fill *opt with the defaults listed above. */
+void fastsv_default_options(fastsv_options* opt);
+
+/* Create a handle on the current CUDA device.  opt may be NULL (defaults).
+ * Errors: FASTSV_ERR_INVALID_ARG (out NULL, bad option), FASTSV_ERR_CUDA. */
+fastsv_status fastsv_create(fastsv_t* out, const fastsv_options* opt);
+
+/* Release the handle and its workspace (synchronises with its last stream). */
+fastsv_status fastsv_destroy(fastsv_t h);
+
+/*
+ * Connected components of one graph (Algorithm 2, Section 3; result as in
+ * Section 3.4).
+ *   n          vertices, 0 <= n <= 2^31 - 1 (n = 0: no work, 0 iterations)
+ *   row_ptr    device, n+1 entries of rowptr_bits width (int32 or int64),
+ *              row_ptr[0] = 0, non-decreasing; m = row_ptr[n] directed entries
+ *   col_idx    device, m int32 neighbour ids (symmetric CSR)
+ *   labels_out device, n int32; receives the smallest vertex id of each
+ *              vertex's component.  It also serves as the parent vector f
+ *              during the solve, so it must not alias row_ptr or col_idx.
+ *   stream     cudaStream_t
+ * Synchronises with `stream` once, to read m = row_ptr[n].  The solve itself
+ * is enqueued; labels_out is valid when the stream reaches the end of it.
+ */
+fastsv_status fastsv_cc(fastsv_t h, int64_t n, const void* row_ptr, const int32_t* col_idx, int32_t* labels_out,
+                        void* stream);
+
+/*
+ * fastsv_cc from host buffers: copies row_ptr and col_idx to handle-owned
+ * device memory, solves, and copies the labels back, all on `stream`, and
+ * returns when labels_host is filled (synchronises).  Host pointers; pinned
+ * memory recommended.  Same sizes and layout as fastsv_cc.
+ */
+fastsv_status fastsv_cc_host(fastsv_t h, int64_t n, const void* row_ptr_host, const int32_t* col_idx_host,
+                             int32_t* labels_host, void* stream);
+
+/*
+ * Connected components of many independent graphs in one solve: Algorithm 2
+ * runs on the disjoint union, and each graph stops at its own early
+ * termination (Section 3.4), so every graph gets exactly the labels and
+ * iteration count it gets alone.
+ *   num_graphs G >= 0
+ *   vtx_off    device int64[G+1]: graph g owns batch vertices [vtx_off[g], vtx_off[g+1]), vtx_off[0] = 0
+ *   edge_off   device int64[G+1]: graph g's entries are col_idx[edge_off[g] .. edge_off[g+1]), edge_off[0] = 0
+ *   row_ptr    device int32[vtx_off[G] + G]: graph g's LOCAL row_ptr (n_g + 1 entries, starting at 0 and
+ *              ending at m_g) at row_ptr[vtx_off[g] + g ...]
+ *   col_idx    device int32[edge_off[G]]: LOCAL neighbour ids of each graph
+ *   labels_out device int32[vtx_off[G]]: LOCAL labels (smallest local id of the component)
+ *   iters_out  device int32[G] or NULL: iterations each graph executed
+ * Synchronises once to read vtx_off[G] and edge_off[G]; the solve is enqueued.
+ */
+fastsv_status fastsv_cc_batched(fastsv_t h, int32_t num_graphs, const int64_t* vtx_off, const int64_t* edge_off,
+                                const int32_t* row_ptr, const int32_t* col_idx, int32_t* labels_out,
+                                int32_t* iters_out, void* stream);
+
+/* Wait for the handle's last call to finish on its stream and report it.
+ * Returns the call's status (FASTSV_OK, FASTSV_ERR_MAX_ITERS, ...). */
+fastsv_status fastsv_get_stats(fastsv_t h, fastsv_stats* out);
+
+/* Human-readable name of a status code (static string). */
+const char* fastsv_status_string(fastsv_status s);
+
+/* Last CUDA runtime error code seen by this handle (0 if none). */
+int32_t fastsv_last_cuda_error(fastsv_t h);
+
+/* Number of kernels this handle has launched so far, counting every kernel
+ * of every iteration of the device-side loop (read after fastsv_get_stats). */
+int64_t fastsv_kernel_launches(fastsv_t h);
+
+/*
+ * Serving pool (continuous batching).  A pool keeps up to max_slots graphs
+ * resident in device memory within hbm_budget_bytes and advances all of them
+ * together: fastsv_pool_step runs `iters` iterations of Algorithm 2 over every
+ * active slot in one device-side loop, so graphs admitted between steps join
+ * the running batch at an iteration boundary.  Each slot stops at its own
+ * early termination (Section 3.4), so a graph's labels and iteration count do
+ * not depend on what else is in the pool.
+ */
+
+/* Create the handle's pool (one per handle). */
+fastsv_status fastsv_pool_create(fastsv_t h, size_t hbm_budget_bytes, int32_t max_slots);
+
+/* Bytes of pool memory a graph with n vertices and m directed entries uses. */
+size_t fastsv_pool_bytes(int64_t n, int64_t m);
+
+/*
+ * Admit one graph: row_ptr_host int32[n+1] and col_idx_host int32[m] (host
+ * memory, pinned recommended, must stay valid until the graph is harvested),
+ * labels_host int32[n] host memory that receives the labels when the slot is
+ * harvested.  The copies to the device are enqueued on the pool's copy
+ * stream.  *slot_out receives the slot id.
+ * Errors: FASTSV_ERR_FULL if no slot or not enough budget is free now (try
+ * again after harvesting), FASTSV_ERR_INVALID_ARG if it can never fit.
+ */
+fastsv_status fastsv_pool_add(fastsv_t h, int64_t n, const int32_t* row_ptr_host, const int32_t* col_idx_host,
+                              int32_t* labels_host, int32_t* slot_out);
+
+/* Advance every active slot by up to `iters` iterations (iters >= 1) on
+ * `stream`.  Slots admitted since the last step join this one (the step
+ * waits for their copies).  Enqueued; returns at once. */
+fastsv_status fastsv_pool_step(fastsv_t h, int32_t iters, void* stream);
+
+/*
+ * Harvest: wait for the last step, copy the labels of up to `cap` slots that
+ * have converged (or hit the iteration cap) into their host buffers, free
+ * those slots, and return their ids in done_slots and iteration counts in
+ * done_iters (may be NULL; a negative count marks a slot stopped by the
+ * iteration cap).  *n_done receives the count; *n_active (may be NULL) the
+ * slots still iterating.  Synchronises.
+ */
+fastsv_status fastsv_pool_poll(fastsv_t h, int32_t* done_slots, int32_t* done_iters, int32_t cap, int32_t* n_done,
+                               int32_t* n_active);
+
+/* Pool occupancy: slots in use and bytes of the budget in use. */
+fastsv_status fastsv_pool_usage(fastsv_t h, int32_t* slots_used, size_t* bytes_used);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FASTSV_H */

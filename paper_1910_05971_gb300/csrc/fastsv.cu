@@ -1,0 +1,608 @@
+// fastsv.cu -- libfastsv: handle, workspace, device-side iteration loop and
+// the single-graph / batched entry points of include/fastsv.h.
+//
+// Every call runs, on the caller's stream:
+//   set-up   segment table, merge-path partition of each graph into hooking
+//            tiles, identity initialisation of f, p, gf (Algorithm 2, first
+//            loop), optional CSR validation;
+//   loop     a CUDA graph whose conditional WHILE node repeats
+//            {k2_hook, k3_grandparent} until no graph's gf changed (the
+//            early termination of Section 3.4) -- no host round trip per
+//            iteration;
+//   finish   per-graph iteration counts and a summary copied to pinned memory.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <climits>
+
+#include "fastsv_internal.h"
+#include "fastsv_kernels.cuh"
+
+using namespace fsv;
+
+namespace fsv {
+
+fastsv_status cuda_fail(fastsv_ctx* h, cudaError_t e) {
+    if (h) h->last_cuda_error = (int)e;
+    (void)cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? FASTSV_ERR_OOM : FASTSV_ERR_CUDA;
+}
+
+fastsv_status dev_alloc(fastsv_ctx* h, void** p, size_t bytes) {
+    *p = nullptr;
+    h->alloc_count++;
+    if (h->opt.fail_alloc_after > 0 && h->alloc_count == h->opt.fail_alloc_after) return FASTSV_ERR_OOM;
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return cuda_fail(h, e);
+    }
+    return FASTSV_OK;
+}
+
+static void dev_free(void** p) {
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+}
+
+static int64_t grow(int64_t need, int64_t cap) {
+    int64_t c = cap + cap / 2;
+    return need > c ? need : c;
+}
+
+fastsv_status ensure_workspace(fastsv_ctx* h, int64_t n, int64_t k2, int64_t k3, int64_t segs) {
+    fastsv_status st;
+    if (segs > h->cap_segs) {
+        dev_free((void**)&h->d_segs);
+        h->cap_segs = 0;
+        int64_t c = grow(segs, h->cap_segs);
+        if ((st = dev_alloc(h, (void**)&h->d_segs, (size_t)c * sizeof(Seg))) != FASTSV_OK) return st;
+        h->cap_segs = c;
+    }
+    if (k2 > h->cap_k2) {
+        dev_free((void**)&h->d_k2_seg);
+        dev_free((void**)&h->d_k2_row);
+        h->cap_k2 = 0;
+        int64_t c = grow(k2 + 1, h->cap_k2);
+        if ((st = dev_alloc(h, (void**)&h->d_k2_seg, (size_t)c * 4)) != FASTSV_OK) return st;
+        if ((st = dev_alloc(h, (void**)&h->d_k2_row, (size_t)c * 4)) != FASTSV_OK) {
+            dev_free((void**)&h->d_k2_seg);
+            return st;
+        }
+        h->cap_k2 = c;
+    }
+    if (k3 > h->cap_k3) {
+        dev_free((void**)&h->d_k3_seg);
+        h->cap_k3 = 0;
+        int64_t c = grow(k3 + 1, h->cap_k3);
+        if ((st = dev_alloc(h, (void**)&h->d_k3_seg, (size_t)c * 4)) != FASTSV_OK) return st;
+        h->cap_k3 = c;
+    }
+    if (n > h->cap_n) {
+        dev_free((void**)&h->d_p);
+        dev_free((void**)&h->d_gf);
+        h->cap_n = 0;
+        int64_t c = n;
+        if ((st = dev_alloc(h, (void**)&h->d_p, (size_t)c * 4)) != FASTSV_OK) return st;
+        if ((st = dev_alloc(h, (void**)&h->d_gf, (size_t)c * 4)) != FASTSV_OK) {
+            dev_free((void**)&h->d_p);
+            return st;
+        }
+        h->cap_n = c;
+    }
+    return FASTSV_OK;
+}
+
+int k2_items(const fastsv_ctx* h) {
+    int it = h->opt.k2_items;
+    return (it == 4 || it == 8 || it == 16) ? it : 8;
+}
+
+// kernel instance selection -------------------------------------------------
+
+static const void* k2_func(int rp64, int items) {
+    if (rp64) {
+        if (items == 4) return (const void*)k2_hook<int64_t, 4>;
+        if (items == 16) return (const void*)k2_hook<int64_t, 16>;
+        return (const void*)k2_hook<int64_t, 8>;
+    }
+    if (items == 4) return (const void*)k2_hook<int32_t, 4>;
+    if (items == 16) return (const void*)k2_hook<int32_t, 16>;
+    return (const void*)k2_hook<int32_t, 8>;
+}
+
+static int k2_smem(int items) {
+    return items == 4 ? k2_smem_bytes<4>() : items == 16 ? k2_smem_bytes<16>() : k2_smem_bytes<8>();
+}
+
+static fastsv_status k2_grid_for(fastsv_ctx* h, int rp64, int items, int* grid) {
+    const void* fn = k2_func(rp64, items);
+    int smem = k2_smem(items);
+    FSV_CUDA(h, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    int per_sm = 0;
+    FSV_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, K2_THREADS, smem));
+    if (per_sm < 1) per_sm = 1;
+    if (h->opt.grid_ctas_per_sm > 0 && h->opt.grid_ctas_per_sm < per_sm) per_sm = h->opt.grid_ctas_per_sm;
+    *grid = per_sm * h->num_sms;
+    return FASTSV_OK;
+}
+
+static fastsv_status k3_grid_for(fastsv_ctx* h, int* grid) {
+    int per_sm = 0;
+    FSV_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k3_grandparent, K3_THREADS, 0));
+    if (per_sm < 1) per_sm = 1;
+    if (h->opt.grid_ctas_per_sm > 0 && h->opt.grid_ctas_per_sm < per_sm) per_sm = h->opt.grid_ctas_per_sm;
+    *grid = per_sm * h->num_sms;
+    return FASTSV_OK;
+}
+
+// the device-side loop: WHILE(cond) { k2_hook; k3_grandparent }
+fastsv_status get_loop_graph(fastsv_ctx* h, int rp64, int items, LoopGraph** out) {
+    GraphKey key{rp64, items, h->opt.mode};
+    auto it = h->graphs.find(key);
+    if (it != h->graphs.end()) {
+        *out = &it->second;
+        return FASTSV_OK;
+    }
+    int g2 = 0, g3 = 0;
+    fastsv_status st;
+    if ((st = k2_grid_for(h, rp64, items, &g2)) != FASTSV_OK) return st;
+    if ((st = k3_grid_for(h, &g3)) != FASTSV_OK) return st;
+    LoopGraph lg;
+    FSV_CUDA(h, cudaGraphCreate(&lg.graph, 0));
+    FSV_CUDA(h, cudaGraphConditionalHandleCreate(&lg.cond, lg.graph, 1, cudaGraphCondAssignDefault));
+    // the struct holds a union of node kinds and has no usable default
+    // constructor: start from zeroed storage
+    alignas(cudaGraphNodeParams) unsigned char cp_storage[sizeof(cudaGraphNodeParams)];
+    memset(cp_storage, 0, sizeof(cp_storage));
+    cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(cp_storage);
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = lg.cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cond_node;
+    FSV_CUDA(h, cudaGraphAddNode(&cond_node, lg.graph, nullptr, nullptr, 0, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+
+    Ctx* ctx = h->d_ctx;
+    cudaGraphConditionalHandle cond = lg.cond;
+    int use_cond = 1;
+    void* k2args[] = {(void*)&ctx, (void*)&cond, (void*)&use_cond};
+    cudaKernelNodeParams kp;
+    memset(&kp, 0, sizeof(kp));
+    kp.func = (void*)k2_func(rp64, items);
+    kp.gridDim = dim3((unsigned)g2);
+    kp.blockDim = dim3(K2_THREADS);
+    kp.sharedMemBytes = (unsigned)k2_smem(items);
+    kp.kernelParams = k2args;
+    cudaGraphNode_t n2, n3;
+    FSV_CUDA(h, cudaGraphAddKernelNode(&n2, body, nullptr, 0, &kp));
+
+    void* k3args[] = {(void*)&ctx, (void*)&cond, (void*)&use_cond};
+    kp.func = (void*)k3_grandparent;
+    kp.gridDim = dim3((unsigned)g3);
+    kp.blockDim = dim3(K3_THREADS);
+    kp.sharedMemBytes = 0;
+    kp.kernelParams = k3args;
+    FSV_CUDA(h, cudaGraphAddKernelNode(&n3, body, &n2, 1, &kp));
+    FSV_CUDA(h, cudaGraphInstantiate(&lg.exec, lg.graph, 0));
+    auto res = h->graphs.emplace(key, lg);
+    *out = &res.first->second;
+    return FASTSV_OK;
+}
+
+fastsv_status run_loop(fastsv_ctx* h, int rp64, int items, cudaStream_t s) {
+    if (h->opt.use_graph) {
+        LoopGraph* lg = nullptr;
+        fastsv_status st = get_loop_graph(h, rp64, items, &lg);
+        if (st != FASTSV_OK) return st;
+        FSV_CUDA(h, cudaGraphLaunch(lg->exec, s));
+        h->pending_loop_kernels = 2;
+        return FASTSV_OK;
+    }
+    // host loop: one synchronisation per iteration, per-kernel event timing
+    int g2 = 0, g3 = 0;
+    fastsv_status st;
+    if ((st = k2_grid_for(h, rp64, items, &g2)) != FASTSV_OK) return st;
+    if ((st = k3_grid_for(h, &g3)) != FASTSV_OK) return st;
+    const void* fn = k2_func(rp64, items);
+    int smem = k2_smem(items);
+    cudaEvent_t e[3];
+    for (int i = 0; i < 3; ++i) FSV_CUDA(h, cudaEventCreate(&e[i]));
+    float t2 = 0.f, t3 = 0.f;
+    int iters = 0;
+    Ctx* ctx = h->d_ctx;
+    cudaGraphConditionalHandle none = 0;
+    int no_cond = 0;
+    int32_t limit = h->opt.max_iters;
+    fastsv_status rc = FASTSV_OK;
+    for (;;) {
+        void* a2[] = {(void*)&ctx, (void*)&none, (void*)&no_cond};
+        void* a3[] = {(void*)&ctx, (void*)&none, (void*)&no_cond};
+        cudaEventRecord(e[0], s);
+        cudaError_t ce = cudaLaunchKernel(fn, dim3(g2), dim3(K2_THREADS), a2, (size_t)smem, s);
+        if (ce == cudaSuccess) ce = cudaEventRecord(e[1], s);
+        if (ce == cudaSuccess) ce = cudaLaunchKernel((const void*)k3_grandparent, dim3(g3), dim3(K3_THREADS), a3, 0, s);
+        if (ce == cudaSuccess) ce = cudaEventRecord(e[2], s);
+        if (ce == cudaSuccess) ce = cudaMemcpyAsync(h->h_scalar, &ctx->any_active, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+        if (ce != cudaSuccess) {
+            rc = cuda_fail(h, ce);
+            break;
+        }
+        h->launches += 2;
+        float a = 0.f, b = 0.f;
+        cudaEventElapsedTime(&a, e[0], e[1]);
+        cudaEventElapsedTime(&b, e[1], e[2]);
+        t2 += a;
+        t3 += b;
+        ++iters;
+        if (*(int32_t*)h->h_scalar == 0 || iters > limit) break;
+    }
+    for (int i = 0; i < 3; ++i) cudaEventDestroy(e[i]);
+    h->ms_k2 = t2;
+    h->ms_k3 = t3;
+    h->pending_loop_kernels = 0;
+    return rc;
+}
+
+static int setup_grid(const fastsv_ctx* h) { return h->num_sms * 8; }
+
+// stream ordering between consecutive calls of one handle
+static void order_after_previous(fastsv_ctx* h, cudaStream_t s) {
+    if (h->pending && h->last_stream != s) cudaStreamWaitEvent(s, h->ev_end, 0);
+}
+
+static fastsv_status finish_call(fastsv_ctx* h, cudaStream_t s, int32_t* iters_out, int64_t n, int64_t m,
+                                 bool single) {
+    k_finish<<<1, 256, 0, s>>>(h->d_ctx, iters_out);
+    h->pending_fixed_launches += 1;
+    FSV_CUDA(h, cudaGetLastError());
+    FSV_CUDA(h, cudaMemcpyAsync(h->h_sum, &h->d_ctx->sum, sizeof(Summary), cudaMemcpyDeviceToHost, s));
+    FSV_CUDA(h, cudaEventRecord(h->ev_end, s));
+    h->pending = true;
+    h->last_stream = s;
+    h->last_n = n;
+    h->last_m = m;
+    h->single = single;
+    return FASTSV_OK;
+}
+
+// validation needs its verdict before any hooking kernel reads the graph
+static fastsv_status run_validation(fastsv_ctx* h, int rp64, cudaStream_t s) {
+    if (!h->opt.validate) return FASTSV_OK;
+    if (rp64)
+        k_validate<int64_t><<<setup_grid(h), 256, 0, s>>>(h->d_ctx, h->opt.validate >= 2);
+    else
+        k_validate<int32_t><<<setup_grid(h), 256, 0, s>>>(h->d_ctx, h->opt.validate >= 2);
+    h->pending_fixed_launches += 1;
+    FSV_CUDA(h, cudaGetLastError());
+    FSV_CUDA(h, cudaMemcpyAsync(h->h_scalar, &h->d_ctx->val_status, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    FSV_CUDA(h, cudaStreamSynchronize(s));
+    if (*(int32_t*)h->h_scalar != 0) {
+        h->launches += h->pending_fixed_launches;
+        h->pending_fixed_launches = 0;
+        h->last_status = FASTSV_ERR_INVALID_GRAPH;
+        h->pending = false;
+        return FASTSV_ERR_INVALID_GRAPH;
+    }
+    return FASTSV_OK;
+}
+
+static fastsv_status solve_single(fastsv_ctx* h, int64_t n, int64_t m, const void* rp, const int32_t* ci,
+                                  int32_t* labels, cudaStream_t s) {
+    const int rp64 = h->opt.rowptr_bits == 64;
+    const int items = k2_items(h);
+    const int64_t tile = (int64_t)K2_THREADS * items;
+    const int64_t t2 = m > 0 ? (n + m + tile - 1) / tile : 0;
+    const int64_t t3 = (n + K3_TILE - 1) / K3_TILE;
+    if (t2 > INT32_MAX || t3 > INT32_MAX) return FASTSV_ERR_UNSUPPORTED;
+    fastsv_status st = ensure_workspace(h, n, t2, t3, 1);
+    if (st != FASTSV_OK) return st;
+    h->pending_fixed_launches = 0;
+    h->ms_k2 = h->ms_k3 = 0.f;
+    FSV_CUDA(h, cudaEventRecord(h->ev_start, s));
+    SingleParams prm;
+    prm.rp = rp;
+    prm.ci = ci;
+    prm.f = labels;
+    prm.p = h->d_p;
+    prm.gf = h->d_gf;
+    prm.n = n;
+    prm.m = m;
+    prm.k2_tile = (int32_t)tile;
+    prm.max_iters = h->opt.max_iters;
+    prm.loop_limit = h->opt.max_iters + 1;
+    WsPtrs ws{h->d_segs, h->d_k2_seg, h->d_k2_row, h->d_k3_seg};
+    k_setup_single<<<1, 1, 0, s>>>(h->d_ctx, prm, ws);
+    if (rp64)
+        k_partition<int64_t><<<setup_grid(h), 256, 0, s>>>(h->d_ctx);
+    else
+        k_partition<int32_t><<<setup_grid(h), 256, 0, s>>>(h->d_ctx);
+    k_init_state<<<setup_grid(h), 256, 0, s>>>(h->d_ctx);
+    h->pending_fixed_launches += 3;
+    FSV_CUDA(h, cudaGetLastError());
+    if ((st = run_validation(h, rp64, s)) != FASTSV_OK) return st;
+    FSV_CUDA(h, cudaEventRecord(h->ev_setup, s));
+    if ((st = run_loop(h, rp64, items, s)) != FASTSV_OK) return st;
+    return finish_call(h, s, nullptr, n, m, true);
+}
+
+}  // namespace fsv
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+
+extern "C" {
+
+void fastsv_default_options(fastsv_options* o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->rowptr_bits = 64;
+    o->mode = FASTSV_MODE_SYNC;
+    o->max_iters = 4096;
+    o->validate = 0;
+    o->use_graph = 1;
+    o->k2_items = 8;
+    o->grid_ctas_per_sm = 0;
+    o->l2_persist = 0;
+    o->timing = 1;
+    o->fail_alloc_after = 0;
+}
+
+const char* fastsv_status_string(fastsv_status s) {
+    switch (s) {
+        case FASTSV_OK: return "FASTSV_OK";
+        case FASTSV_ERR_INVALID_ARG: return "FASTSV_ERR_INVALID_ARG";
+        case FASTSV_ERR_OOM: return "FASTSV_ERR_OOM";
+        case FASTSV_ERR_CUDA: return "FASTSV_ERR_CUDA";
+        case FASTSV_ERR_MAX_ITERS: return "FASTSV_ERR_MAX_ITERS";
+        case FASTSV_ERR_TIMEOUT: return "FASTSV_ERR_TIMEOUT";
+        case FASTSV_ERR_UNSUPPORTED: return "FASTSV_ERR_UNSUPPORTED";
+        case FASTSV_ERR_INVALID_GRAPH: return "FASTSV_ERR_INVALID_GRAPH";
+        case FASTSV_ERR_FULL: return "FASTSV_ERR_FULL";
+    }
+    return "FASTSV_UNKNOWN";
+}
+
+fastsv_status fastsv_create(fastsv_t* out, const fastsv_options* opt) {
+    if (!out) return FASTSV_ERR_INVALID_ARG;
+    *out = nullptr;
+    fastsv_options o;
+    if (opt)
+        o = *opt;
+    else
+        fastsv_default_options(&o);
+    if (o.rowptr_bits != 32 && o.rowptr_bits != 64) return FASTSV_ERR_INVALID_ARG;
+    if (o.mode != FASTSV_MODE_SYNC && o.mode != FASTSV_MODE_ASYNC) return FASTSV_ERR_INVALID_ARG;
+    if (o.max_iters < 1 || o.max_iters > (1 << 30)) return FASTSV_ERR_INVALID_ARG;
+    if (o.validate < 0 || o.validate > 2) return FASTSV_ERR_INVALID_ARG;
+    if (o.mode == FASTSV_MODE_ASYNC) return FASTSV_ERR_UNSUPPORTED;
+    fastsv_ctx* h = new fastsv_ctx();
+    h->opt = o;
+    fastsv_status st = FASTSV_OK;
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->d_ctx, sizeof(Ctx));
+    if (e == cudaSuccess) e = cudaMemset(h->d_ctx, 0, sizeof(Ctx));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&h->h_sum, sizeof(Summary));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&h->h_scalar, 64);
+    if (e == cudaSuccess) e = cudaEventCreate(&h->ev_start);
+    if (e == cudaSuccess) e = cudaEventCreate(&h->ev_setup);
+    if (e == cudaSuccess) e = cudaEventCreate(&h->ev_end);
+    if (e != cudaSuccess) {
+        st = cuda_fail(h, e);
+        fastsv_destroy(h);
+        return st;
+    }
+    memset(h->h_sum, 0, sizeof(Summary));
+    *out = h;
+    return FASTSV_OK;
+}
+
+fastsv_status fastsv_destroy(fastsv_t h) {
+    if (!h) return FASTSV_ERR_INVALID_ARG;
+    if (h->pending && h->ev_end) cudaEventSynchronize(h->ev_end);
+    pool_release(h);
+    for (auto& kv : h->graphs) {
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+    }
+    dev_free((void**)&h->d_ctx);
+    dev_free((void**)&h->d_segs);
+    dev_free((void**)&h->d_k2_seg);
+    dev_free((void**)&h->d_k2_row);
+    dev_free((void**)&h->d_k3_seg);
+    dev_free((void**)&h->d_p);
+    dev_free((void**)&h->d_gf);
+    dev_free(&h->d_rp_copy);
+    dev_free((void**)&h->d_ci_copy);
+    dev_free((void**)&h->d_lab_copy);
+    if (h->h_sum) cudaFreeHost(h->h_sum);
+    if (h->h_scalar) cudaFreeHost(h->h_scalar);
+    if (h->ev_start) cudaEventDestroy(h->ev_start);
+    if (h->ev_setup) cudaEventDestroy(h->ev_setup);
+    if (h->ev_end) cudaEventDestroy(h->ev_end);
+    delete h;
+    return FASTSV_OK;
+}
+
+static void record_empty_call(fastsv_ctx* h, int64_t n, int64_t m) {
+    h->pending = false;
+    h->last_status = FASTSV_OK;
+    h->last_n = n;
+    h->last_m = m;
+    memset(h->h_sum, 0, sizeof(Summary));
+    h->h_sum->converged = 1;
+}
+
+fastsv_status fastsv_cc(fastsv_t h, int64_t n, const void* row_ptr, const int32_t* col_idx, int32_t* labels_out,
+                        void* stream) {
+    if (!h || n < 0 || n > (int64_t)INT32_MAX) return FASTSV_ERR_INVALID_ARG;
+    if (n == 0) {
+        record_empty_call(h, 0, 0);
+        return FASTSV_OK;
+    }
+    if (!row_ptr || !labels_out) return FASTSV_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    order_after_previous(h, s);
+    const int w = h->opt.rowptr_bits / 8;
+    FSV_CUDA(h, cudaMemcpyAsync(h->h_scalar, (const char*)row_ptr + (size_t)n * w, (size_t)w,
+                                cudaMemcpyDeviceToHost, s));
+    FSV_CUDA(h, cudaStreamSynchronize(s));
+    int64_t m = w == 8 ? *(int64_t*)h->h_scalar : (int64_t) * (int32_t*)h->h_scalar;
+    if (m < 0) return FASTSV_ERR_INVALID_GRAPH;
+    if (m > 0 && !col_idx) return FASTSV_ERR_INVALID_ARG;
+    return solve_single(h, n, m, row_ptr, col_idx, labels_out, s);
+}
+
+static fastsv_status ensure_copy(fastsv_ctx* h, void** buf, size_t* cap, size_t bytes) {
+    if (bytes <= *cap && *buf) return FASTSV_OK;
+    dev_free(buf);
+    *cap = 0;
+    fastsv_status st = dev_alloc(h, buf, bytes);
+    if (st == FASTSV_OK) *cap = bytes;
+    return st;
+}
+
+fastsv_status fastsv_get_stats(fastsv_t h, fastsv_stats* out);
+
+fastsv_status fastsv_cc_host(fastsv_t h, int64_t n, const void* row_ptr_host, const int32_t* col_idx_host,
+                             int32_t* labels_host, void* stream) {
+    if (!h || n < 0 || n > (int64_t)INT32_MAX) return FASTSV_ERR_INVALID_ARG;
+    if (n == 0) {
+        record_empty_call(h, 0, 0);
+        return FASTSV_OK;
+    }
+    if (!row_ptr_host || !labels_host) return FASTSV_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    order_after_previous(h, s);
+    const int w = h->opt.rowptr_bits / 8;
+    int64_t m = w == 8 ? ((const int64_t*)row_ptr_host)[n] : (int64_t)((const int32_t*)row_ptr_host)[n];
+    if (m < 0) return FASTSV_ERR_INVALID_GRAPH;
+    if (m > 0 && !col_idx_host) return FASTSV_ERR_INVALID_ARG;
+    fastsv_status st;
+    if ((st = ensure_copy(h, &h->d_rp_copy, &h->cap_rp_copy, (size_t)(n + 1) * w)) != FASTSV_OK) return st;
+    if ((st = ensure_copy(h, (void**)&h->d_ci_copy, &h->cap_ci_copy, (size_t)(m > 0 ? m : 1) * 4)) != FASTSV_OK)
+        return st;
+    if ((st = ensure_copy(h, (void**)&h->d_lab_copy, &h->cap_lab_copy, (size_t)n * 4)) != FASTSV_OK) return st;
+    FSV_CUDA(h, cudaMemcpyAsync(h->d_rp_copy, row_ptr_host, (size_t)(n + 1) * w, cudaMemcpyHostToDevice, s));
+    if (m > 0) FSV_CUDA(h, cudaMemcpyAsync(h->d_ci_copy, col_idx_host, (size_t)m * 4, cudaMemcpyHostToDevice, s));
+    if ((st = solve_single(h, n, m, h->d_rp_copy, h->d_ci_copy, h->d_lab_copy, s)) != FASTSV_OK) return st;
+    FSV_CUDA(h, cudaMemcpyAsync(labels_host, h->d_lab_copy, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
+    FSV_CUDA(h, cudaStreamSynchronize(s));
+    fastsv_stats tmp;
+    return fastsv_get_stats(h, &tmp);
+}
+
+fastsv_status fastsv_cc_batched(fastsv_t h, int32_t G, const int64_t* vtx_off, const int64_t* edge_off,
+                                const int32_t* row_ptr, const int32_t* col_idx, int32_t* labels_out,
+                                int32_t* iters_out, void* stream) {
+    if (!h || G < 0) return FASTSV_ERR_INVALID_ARG;
+    if (G == 0) {
+        record_empty_call(h, 0, 0);
+        return FASTSV_OK;
+    }
+    if (!vtx_off || !edge_off || !row_ptr || !labels_out) return FASTSV_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    order_after_previous(h, s);
+    FSV_CUDA(h, cudaMemcpyAsync(h->h_scalar, vtx_off + G, 8, cudaMemcpyDeviceToHost, s));
+    FSV_CUDA(h, cudaMemcpyAsync(h->h_scalar + 1, edge_off + G, 8, cudaMemcpyDeviceToHost, s));
+    FSV_CUDA(h, cudaStreamSynchronize(s));
+    const int64_t N = h->h_scalar[0], M = h->h_scalar[1];
+    if (N < 0 || M < 0) return FASTSV_ERR_INVALID_GRAPH;
+    if (M > 0 && !col_idx) return FASTSV_ERR_INVALID_ARG;
+    const int items = k2_items(h);
+    const int64_t tile = (int64_t)K2_THREADS * items;
+    const int64_t t2 = (N + M) / tile + G + 1;
+    const int64_t t3 = N / K3_TILE + G + 1;
+    if (t2 > INT32_MAX || t3 > INT32_MAX) return FASTSV_ERR_UNSUPPORTED;
+    fastsv_status st = ensure_workspace(h, N > 0 ? N : 1, t2, t3, G);
+    if (st != FASTSV_OK) return st;
+    h->pending_fixed_launches = 0;
+    h->ms_k2 = h->ms_k3 = 0.f;
+    FSV_CUDA(h, cudaEventRecord(h->ev_start, s));
+    BatchParams prm;
+    prm.G = G;
+    prm.vtx_off = vtx_off;
+    prm.edge_off = edge_off;
+    prm.row_ptr = row_ptr;
+    prm.col_idx = col_idx;
+    prm.labels = labels_out;
+    prm.p = h->d_p;
+    prm.gf = h->d_gf;
+    prm.k2_tile = (int32_t)tile;
+    prm.max_iters = h->opt.max_iters;
+    prm.loop_limit = h->opt.max_iters + 1;
+    WsPtrs ws{h->d_segs, h->d_k2_seg, h->d_k2_row, h->d_k3_seg};
+    int gs = (G + 255) / 256;
+    if (gs > setup_grid(h)) gs = setup_grid(h);
+    k_setup_batched<<<gs, 256, 0, s>>>(h->d_ctx, prm, ws);
+    k_scan_tiles<<<1, 1024, 0, s>>>(h->d_ctx);
+    k_partition<int32_t><<<setup_grid(h), 256, 0, s>>>(h->d_ctx);
+    k_init_state<<<setup_grid(h), 256, 0, s>>>(h->d_ctx);
+    h->pending_fixed_launches += 4;
+    FSV_CUDA(h, cudaGetLastError());
+    if ((st = run_validation(h, 0, s)) != FASTSV_OK) return st;
+    FSV_CUDA(h, cudaEventRecord(h->ev_setup, s));
+    if (N > 0) {
+        if ((st = run_loop(h, 0, items, s)) != FASTSV_OK) return st;
+    } else {
+        h->pending_loop_kernels = 0;
+    }
+    return finish_call(h, s, iters_out, N, M, false);
+}
+
+fastsv_status fastsv_get_stats(fastsv_t h, fastsv_stats* out) {
+    if (!h || !out) return FASTSV_ERR_INVALID_ARG;
+    memset(out, 0, sizeof(*out));
+    float total = 0.f, setup = 0.f;
+    if (h->pending) {
+        cudaError_t e = cudaEventSynchronize(h->ev_end);
+        if (e != cudaSuccess) {
+            h->pending = false;
+            return cuda_fail(h, e);
+        }
+        h->pending = false;
+        const Summary& S = *h->h_sum;
+        h->launches += h->pending_fixed_launches + (int64_t)h->pending_loop_kernels * S.loop_iter;
+        h->pending_fixed_launches = 0;
+        int st = FASTSV_OK;
+        if (S.status & (DEV_ERR_BAD_ROWPTR | DEV_ERR_BAD_COLIDX | DEV_ERR_ASYMMETRIC))
+            st = FASTSV_ERR_INVALID_GRAPH;
+        else if (S.status & DEV_ERR_MAX_ITERS)
+            st = FASTSV_ERR_MAX_ITERS;
+        h->last_status = st;
+        if (h->opt.timing) {
+            cudaEventElapsedTime(&total, h->ev_start, h->ev_end);
+            cudaEventElapsedTime(&setup, h->ev_start, h->ev_setup);
+        }
+        h->h_sum->iterations = S.iterations;  // keep for repeated queries
+        out->ms_total = total;
+        out->ms_setup = setup;
+        h->ms_total_cache = total;
+        h->ms_setup_cache = setup;
+    } else {
+        out->ms_total = h->ms_total_cache;
+        out->ms_setup = h->ms_setup_cache;
+    }
+    const Summary& S = *h->h_sum;
+    out->n = h->last_n;
+    out->m = h->last_m;
+    out->iterations = S.iterations;
+    out->status = h->last_status;
+    out->converged = S.converged;
+    out->ms_k2 = h->ms_k2;
+    out->ms_k3 = h->ms_k3;
+    int len = (int)(S.iterations < TRACE_LEN ? S.iterations : TRACE_LEN);
+    out->trace_len = h->single ? len : 0;
+    for (int i = 0; i < out->trace_len; ++i) out->changed_per_iter[i] = (int64_t)S.trace[i];
+    return (fastsv_status)h->last_status;
+}
+
+int32_t fastsv_last_cuda_error(fastsv_t h) { return h ? h->last_cuda_error : 0; }
+
+int64_t fastsv_kernel_launches(fastsv_t h) { return h ? h->launches : 0; }
+
+}  // extern "C"

@@ -1,0 +1,106 @@
+// fastsv_internal.h -- host-side handle shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <map>
+#include <vector>
+
+#include "../../include/fastsv.h"
+#include "fastsv_types.cuh"
+
+namespace fsv {
+
+struct GraphKey {
+    int rp64;
+    int items;
+    int mode;
+    bool operator<(const GraphKey& o) const {
+        if (rp64 != o.rp64) return rp64 < o.rp64;
+        if (items != o.items) return items < o.items;
+        return mode < o.mode;
+    }
+};
+
+struct LoopGraph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphConditionalHandle cond = 0;
+};
+
+struct Pool;  // serving pool (pool.cu)
+
+}  // namespace fsv
+
+struct fastsv_ctx {
+    fastsv_options opt;
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t last_stream = nullptr;
+
+    // device context and workspace
+    fsv::Ctx* d_ctx = nullptr;
+    fsv::Seg* d_segs = nullptr;
+    int64_t cap_segs = 0;
+    int32_t* d_k2_seg = nullptr;
+    int32_t* d_k2_row = nullptr;
+    int64_t cap_k2 = 0;
+    int32_t* d_k3_seg = nullptr;
+    int64_t cap_k3 = 0;
+    int32_t* d_p = nullptr;
+    int32_t* d_gf = nullptr;
+    int64_t cap_n = 0;
+
+    // device copies for the host-buffer entry point
+    void* d_rp_copy = nullptr;
+    size_t cap_rp_copy = 0;
+    int32_t* d_ci_copy = nullptr;
+    size_t cap_ci_copy = 0;
+    int32_t* d_lab_copy = nullptr;
+    size_t cap_lab_copy = 0;
+
+    // pinned host staging
+    fsv::Summary* h_sum = nullptr;
+    int64_t* h_scalar = nullptr;
+
+    cudaEvent_t ev_start = nullptr, ev_setup = nullptr, ev_end = nullptr;
+    bool have_timing = false;
+
+    std::map<fsv::GraphKey, fsv::LoopGraph> graphs;
+    int k2_grid = 0, k3_grid = 0;
+
+    // bookkeeping of the last call
+    int64_t last_n = 0, last_m = 0;
+    int last_status = 0;
+    int last_cuda_error = 0;
+    bool pending = false;      // a call whose summary has not been read yet
+    bool single = true;        // last call was a single-graph call
+    float ms_k2 = 0.f, ms_k3 = 0.f;
+    float ms_total_cache = 0.f, ms_setup_cache = 0.f;
+    int64_t launches = 0;      // kernels launched, settled by fastsv_get_stats
+    int64_t pending_fixed_launches = 0;  // set-up kernels of the pending call
+    int pending_loop_kernels = 0;        // kernels per device-loop iteration of the pending call
+    int alloc_count = 0;
+
+    fsv::Pool* pool = nullptr;
+};
+
+namespace fsv {
+
+// error plumbing
+fastsv_status cuda_fail(fastsv_ctx* h, cudaError_t e);
+#define FSV_CUDA(h, call)                                  \
+    do {                                                   \
+        cudaError_t _e = (call);                           \
+        if (_e != cudaSuccess) return fsv::cuda_fail(h, _e); \
+    } while (0)
+
+// device allocation through the handle (counts allocations for the test hook)
+fastsv_status dev_alloc(fastsv_ctx* h, void** p, size_t bytes);
+fastsv_status ensure_workspace(fastsv_ctx* h, int64_t n, int64_t k2_tiles, int64_t k3_tiles, int64_t segs);
+fastsv_status get_loop_graph(fastsv_ctx* h, int rp64, int items, LoopGraph** out);
+fastsv_status run_loop(fastsv_ctx* h, int rp64, int items, cudaStream_t s);
+int k2_items(const fastsv_ctx* h);
+void pool_release(fastsv_ctx* h);
+
+}  // namespace fsv

@@ -1,0 +1,571 @@
+// fastsv_kernels.cuh -- device code of the FastSV iteration (sm_103a).
+//
+// Method: Zhang, Azad, Hu, "FastSV: A Distributed-Memory Connected Component
+// Algorithm with Fast Convergence" (arXiv:1910.05971), Algorithm 2 (Section 3)
+// in the vector form of Algorithm 3 (Section 4.1).
+//
+// Device state of one graph ("segment"):
+//   p   snapshot of the parent vector f at the start of an iteration
+//       (read-only while hooking: plays the role of "f" in Algorithm 2)
+//   f   the parent vector being updated (plays "f_next"); equal to p at the
+//       start of every iteration; every write is an atomic min
+//   gf  grandparents p[p] (Algorithm 3's gf), recomputed after each iteration
+//
+// One iteration = two kernels:
+//   k2_hook        mngf[u] = min_{v in N(u)} gf[v] (the (select2nd,min) SpMV),
+//                  then f[p[u]] min= mngf[u]          (stochastic hooking)
+//                  and  f[u] min= min(mngf[u], gf[u]) (aggressive hooking +
+//                  shortcutting).  Work is split by merge-path tiles over
+//                  (rows + entries), so every CTA gets the same amount of
+//                  work whatever the degree distribution, reads a contiguous
+//                  slice of col_idx, and a hub row simply spans several
+//                  tiles: each tile hooks with the minimum over its part of
+//                  the row, which is exact because every hook is a min.
+//   k3_grandparent gf'[u] = f[f[u]], count gf' != gf (the termination test of
+//                  Section 3.4 / Algorithm 3's ISNE + reduce), gf = gf',
+//                  p = f.  The last CTA to finish advances every segment's
+//                  iteration counter, retires segments whose count is zero,
+//                  and sets the CUDA-graph WHILE condition.
+// Because hooks are atomic mins of values that depend only on (p, gf), the
+// result of an iteration does not depend on thread scheduling: the device
+// reproduces the sequential pointer graph of Algorithm 2 bit for bit.
+#pragma once
+
+#include "fastsv_types.cuh"
+
+namespace fsv {
+
+// ---------------------------------------------------------------------------
+// small helpers
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ int32_t ld_stream(const int32_t* p) { return __ldcs(p); }
+__device__ __forceinline__ int64_t ld_stream(const int64_t* p) { return (int64_t)__ldcs((const long long*)p); }
+
+template <typename RP>
+__device__ __forceinline__ int64_t rp_at(const RP* rp, int64_t i) { return (int64_t)rp[i]; }
+
+// number of rows i in [0, n) whose merge-path row-end position rp[i+1] + i is
+// < d (rows fully consumed before diagonal d); Merrill & Garland's merge-path
+// search specialised to "row ends vs. entry indices".
+template <typename RP>
+__device__ __forceinline__ int64_t merge_path_rows(const RP* rp, int64_t n, int64_t m, int64_t d) {
+    int64_t lo = d > m ? d - m : 0;
+    int64_t hi = d < n ? d : n;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (rp_at(rp, mid + 1) + mid < d)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int segment_of(const Seg* segs, int nsegs, int64_t t, bool k2) {
+    int lo = 0, hi = nsegs - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        int64_t start = k2 ? segs[mid].k2_tile0 : segs[mid].k3_tile0;
+        if (start <= t)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// ---------------------------------------------------------------------------
+// set-up kernels (once per call)
+// ---------------------------------------------------------------------------
+
+// workspace pointers owned by the handle, written into the context every call
+struct WsPtrs {
+    Seg* segs;
+    int32_t* k2_seg;
+    int32_t* k2_row;
+    int32_t* k3_seg;
+};
+
+__device__ __forceinline__ void set_ws(Ctx* ctx, const WsPtrs& ws) {
+    ctx->segs = ws.segs;
+    ctx->k2_tile_seg = ws.k2_seg;
+    ctx->k2_tile_row = ws.k2_row;
+    ctx->k3_tile_seg = ws.k3_seg;
+}
+
+struct SingleParams {
+    const void* rp;
+    const int32_t* ci;
+    int32_t* f;
+    int32_t* p;
+    int32_t* gf;
+    int64_t n, m;
+    int32_t k2_tile;
+    int32_t max_iters;
+    int32_t loop_limit;
+};
+
+// one graph: segment 0 and the call's scalars
+__global__ void k_setup_single(Ctx* ctx, SingleParams prm, WsPtrs ws) {
+    set_ws(ctx, ws);
+    Seg s;
+    s.rp = prm.rp;
+    s.ci = prm.ci;
+    s.f = prm.f;
+    s.p = prm.p;
+    s.gf = prm.gf;
+    s.n = prm.n;
+    s.m = prm.m;
+    s.k2_tile0 = 0;
+    s.k3_tile0 = 0;
+    s.k2_ntiles = prm.m > 0 ? (int32_t)((prm.n + prm.m + prm.k2_tile - 1) / prm.k2_tile) : 0;
+    s.k3_ntiles = (int32_t)((prm.n + K3_TILE - 1) / K3_TILE);
+    s.active = prm.n > 0;
+    s.iters = 0;
+    s.status = 0;
+    s.converged = 0;
+    s.changed = 0;
+    s.user = 0;
+    ws.segs[0] = s;
+    ctx->num_segs = 1;
+    ctx->k2_tile = prm.k2_tile;
+    ctx->k2_total = s.k2_ntiles;
+    ctx->k3_total = s.k3_ntiles;
+    ctx->max_iters = prm.max_iters;
+    ctx->loop_limit = prm.loop_limit;
+    ctx->loop_iter = 0;
+    ctx->k3_done = 0;
+    ctx->any_active = s.active;
+    ctx->val_status = 0;
+    for (int i = 0; i < TRACE_LEN; ++i) ctx->sum.trace[i] = 0;
+}
+
+struct BatchParams {
+    int32_t G;
+    const int64_t* vtx_off;
+    const int64_t* edge_off;
+    const int32_t* row_ptr;
+    const int32_t* col_idx;
+    int32_t* labels;
+    int32_t* p;
+    int32_t* gf;
+    int32_t k2_tile;
+    int32_t max_iters;
+    int32_t loop_limit;
+};
+
+// many graphs: one segment per graph (tile counts; offsets come from k_scan_tiles)
+__global__ void k_setup_batched(Ctx* ctx, BatchParams prm, WsPtrs ws) {
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < prm.G; g += (int64_t)gridDim.x * blockDim.x) {
+        int64_t v0 = prm.vtx_off[g], v1 = prm.vtx_off[g + 1];
+        int64_t e0 = prm.edge_off[g], e1 = prm.edge_off[g + 1];
+        int64_t n = v1 - v0, m = e1 - e0;
+        if (n < 0) n = 0;
+        if (m < 0) m = 0;
+        Seg s;
+        s.rp = prm.row_ptr + v0 + g;
+        s.ci = prm.col_idx + e0;
+        s.f = prm.labels + v0;
+        s.p = prm.p + v0;
+        s.gf = prm.gf + v0;
+        s.n = n;
+        s.m = m;
+        s.k2_tile0 = 0;
+        s.k3_tile0 = 0;
+        s.k2_ntiles = (m > 0 && n > 0) ? (int32_t)((n + m + prm.k2_tile - 1) / prm.k2_tile) : 0;
+        s.k3_ntiles = (int32_t)((n + K3_TILE - 1) / K3_TILE);
+        s.active = n > 0;
+        s.iters = 0;
+        s.status = 0;
+        s.converged = n == 0;
+        s.changed = 0;
+        s.user = (int32_t)g;
+        ws.segs[g] = s;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        set_ws(ctx, ws);
+        ctx->num_segs = prm.G;
+        ctx->k2_tile = prm.k2_tile;
+        ctx->max_iters = prm.max_iters;
+        ctx->loop_limit = prm.loop_limit;
+        ctx->loop_iter = 0;
+        ctx->k3_done = 0;
+        ctx->val_status = 0;
+        for (int i = 0; i < TRACE_LEN; ++i) ctx->sum.trace[i] = 0;
+    }
+}
+
+// exclusive prefix sums of the per-segment tile counts (one CTA of 1024
+// threads, each owning a contiguous chunk of segments)
+__global__ void __launch_bounds__(1024) k_scan_tiles(Ctx* ctx) {
+    __shared__ long long s2[1024], s3[1024];
+    __shared__ int s_any[1024];
+    const int G = ctx->num_segs;
+    Seg* segs = ctx->segs;
+    const int tid = threadIdx.x;
+    const int chunk = (G + 1023) / 1024;
+    const int b = tid * chunk, e = min(G, b + chunk);
+    long long a2 = 0, a3 = 0;
+    int any = 0;
+    for (int g = b; g < e; ++g) {
+        a2 += segs[g].k2_ntiles;
+        a3 += segs[g].k3_ntiles;
+        any |= segs[g].active;
+    }
+    s2[tid] = a2;
+    s3[tid] = a3;
+    s_any[tid] = any;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        long long v2 = tid >= off ? s2[tid - off] : 0, v3 = tid >= off ? s3[tid - off] : 0;
+        int va = tid >= off ? s_any[tid - off] : 0;
+        __syncthreads();
+        s2[tid] += v2;
+        s3[tid] += v3;
+        s_any[tid] |= va;
+        __syncthreads();
+    }
+    long long o2 = s2[tid] - a2, o3 = s3[tid] - a3;
+    for (int g = b; g < e; ++g) {
+        segs[g].k2_tile0 = o2;
+        segs[g].k3_tile0 = o3;
+        o2 += segs[g].k2_ntiles;
+        o3 += segs[g].k3_ntiles;
+    }
+    if (tid == 1023) {
+        ctx->k2_total = s2[1023];
+        ctx->k3_total = s3[1023];
+        ctx->any_active = s_any[1023];
+    }
+}
+
+// merge-path start row of every hooking tile, and the segment of every tile
+template <typename RP>
+__global__ void k_partition(Ctx* ctx) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const Seg* segs = ctx->segs;
+    const int G = ctx->num_segs;
+    const int64_t tile = ctx->k2_tile;
+    for (int64_t t = t0; t < ctx->k2_total; t += stride) {
+        int s = segment_of(segs, G, t, true);
+        const Seg& S = segs[s];
+        int64_t d = (t - S.k2_tile0) * tile;
+        ctx->k2_tile_seg[t] = s;
+        ctx->k2_tile_row[t] = (int32_t)merge_path_rows((const RP*)S.rp, S.n, S.m, d);
+    }
+    for (int64_t t = t0; t < ctx->k3_total; t += stride) ctx->k3_tile_seg[t] = segment_of(segs, G, t, false);
+}
+
+// f = p = gf = local identity (Algorithm 2: f[u] <- u; Algorithm 3: gf = dup(f))
+__global__ void k_init_state(Ctx* ctx) {
+    const int64_t total = ctx->k3_total;
+    for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
+        const Seg& S = ctx->segs[ctx->k3_tile_seg[t]];
+        int64_t v0 = (t - S.k3_tile0) * K3_TILE;
+        int64_t v1 = min(v0 + K3_TILE, S.n);
+        for (int64_t v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
+            S.f[v] = (int32_t)v;
+            S.p[v] = (int32_t)v;
+            S.gf[v] = (int32_t)v;
+        }
+    }
+}
+
+// CSR validation: row_ptr[0] = 0, non-decreasing, row_ptr[n] = m; every
+// neighbour id in [0, n); with check_sym, (v,u) present for every (u,v)
+// (binary search, rows must be sorted).  Sets ctx->val_status bits.
+template <typename RP>
+__global__ void k_validate(Ctx* ctx, int check_sym) {
+    const int64_t total = ctx->k3_total;
+    int32_t bad = 0;
+    for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
+        const Seg& S = ctx->segs[ctx->k3_tile_seg[t]];
+        const RP* rp = (const RP*)S.rp;
+        int64_t v0 = (t - S.k3_tile0) * K3_TILE;
+        int64_t v1 = min(v0 + K3_TILE, S.n);
+        for (int64_t v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
+            int64_t a = rp_at(rp, v), b = rp_at(rp, v + 1);
+            if (v == 0 && a != 0) bad |= DEV_ERR_BAD_ROWPTR;
+            if (b < a || a < 0 || b > S.m) {
+                bad |= DEV_ERR_BAD_ROWPTR;
+                continue;
+            }
+            if (v + 1 == S.n && b != S.m) bad |= DEV_ERR_BAD_ROWPTR;
+            for (int64_t e = a; e < b; ++e) {
+                int32_t w = S.ci[e];
+                if (w < 0 || w >= S.n) {
+                    bad |= DEV_ERR_BAD_COLIDX;
+                    break;
+                }
+                if (check_sym) {
+                    int64_t lo = rp_at(rp, w), hi = rp_at(rp, w + 1);
+                    if (hi < lo || lo < 0 || hi > S.m) {
+                        bad |= DEV_ERR_BAD_ROWPTR;
+                        break;
+                    }
+                    while (lo < hi) {
+                        int64_t mid = (lo + hi) >> 1;
+                        if (S.ci[mid] < (int32_t)v)
+                            lo = mid + 1;
+                        else
+                            hi = mid;
+                    }
+                    if (lo >= rp_at(rp, w + 1) || S.ci[lo] != (int32_t)v) bad |= DEV_ERR_ASYMMETRIC;
+                }
+            }
+        }
+    }
+    if (bad) atomicOr(&ctx->val_status, bad);
+}
+
+// ---------------------------------------------------------------------------
+// K2: SpMV (select2nd, min) fused with the three hooks
+// ---------------------------------------------------------------------------
+
+template <int ITEMS>
+constexpr int k2_smem_bytes() {
+    return (2 * (K2_THREADS * ITEMS + 1) + K2_THREADS * ITEMS) * (int)sizeof(int32_t);
+}
+
+template <typename RP, int ITEMS>
+__global__ void __launch_bounds__(K2_THREADS)
+    k2_hook(Ctx* __restrict__ ctx, cudaGraphConditionalHandle cond, int use_cond) {
+    constexpr int TILE = K2_THREADS * ITEMS;
+    // The loop condition starts every iteration at "stop"; only the last CTA
+    // of k3_grandparent sets it back to "continue" when work remains, so a
+    // device loop can never outlive its iteration bookkeeping.
+    if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
+    extern __shared__ int32_t smem[];
+    int32_t* s_rowend = smem;                 // local end offset of each row in the tile
+    int32_t* s_mngf = smem + (TILE + 1);      // per-row minimum over the tile's entries
+    int32_t* s_val = smem + 2 * (TILE + 1);   // gf[col_idx[e]] for the tile's entries
+    const int tid = threadIdx.x;
+    const int64_t T = ctx->k2_total;
+    const int32_t* __restrict__ tile_seg = ctx->k2_tile_seg;
+    const int32_t* __restrict__ tile_row = ctx->k2_tile_row;
+    const Seg* __restrict__ segs = ctx->segs;
+
+    for (int64_t t = blockIdx.x; t < T; t += gridDim.x) {
+        const Seg* S = segs + tile_seg[t];
+        if (!S->active) continue;
+        const RP* __restrict__ rp = (const RP*)S->rp;
+        const int32_t* __restrict__ ci = S->ci;
+        const int32_t* __restrict__ gf = S->gf;
+        const int32_t* __restrict__ p = S->p;
+        int32_t* f = S->f;
+        const int64_t n = S->n, m = S->m;
+        const int64_t lt = t - S->k2_tile0;
+        const int64_t d0 = lt * TILE;
+        const int64_t d1 = min(d0 + (int64_t)TILE, n + m);
+        const int64_t x0 = tile_row[t];
+        const int64_t x1 = (lt + 1 < S->k2_ntiles) ? (int64_t)tile_row[t + 1] : n;
+        if (x1 < x0) continue;  // only possible for a malformed row_ptr
+        const int64_t y0 = d0 - x0, y1 = d1 - x1;
+        const int nfull = (int)(x1 - x0);            // rows whose end lies in this tile
+        const int R = nfull + (x1 < n ? 1 : 0);       // plus the row still open at the tile end
+        const int E = (int)(y1 - y0);                 // entries in this tile
+        const int D = (int)(d1 - d0);
+
+        // phase 1: row ends, and the gathered grandparents of the tile's entries
+        for (int i = tid; i < R; i += K2_THREADS) {
+            int64_t e = rp_at(rp, x0 + i + 1);
+            e = e < y1 ? e : y1;
+            e -= y0;
+            s_rowend[i] = (int32_t)(e < 0 ? 0 : e);
+            s_mngf[i] = INF;
+        }
+        {
+            int32_t c[ITEMS];
+#pragma unroll
+            for (int q = 0; q < ITEMS; ++q) {
+                int j = tid + q * K2_THREADS;
+                c[q] = j < E ? ld_stream(ci + y0 + j) : -1;
+            }
+#pragma unroll
+            for (int q = 0; q < ITEMS; ++q) {
+                int j = tid + q * K2_THREADS;
+                if (j < E) s_val[j] = ((uint32_t)c[q] < (uint64_t)n) ? __ldg(gf + c[q]) : INF;
+            }
+        }
+        __syncthreads();
+
+        // phase 2: every thread walks ITEMS consecutive merge-path items
+        // (row ends and entries) and min-reduces entries per row
+        const int k0 = tid * ITEMS;
+        if (k0 < D) {
+            int lo = 0, hi = nfull;
+            while (lo < hi) {
+                int mid = (lo + hi) >> 1;
+                if (s_rowend[mid] + mid < k0)
+                    lo = mid + 1;
+                else
+                    hi = mid;
+            }
+            int r = lo, y = k0 - lo;
+            int32_t acc = INF;
+            const int kend = min(k0 + ITEMS, D);
+            for (int k = k0; k < kend; ++k) {
+                if (r < nfull && y >= s_rowend[r]) {
+                    if (acc != INF) atomicMin(&s_mngf[r], acc);
+                    acc = INF;
+                    ++r;
+                } else {
+                    acc = min(acc, s_val[y < E ? y : E - 1]);
+                    ++y;
+                }
+            }
+            if (acc != INF && r < R) atomicMin(&s_mngf[r], acc);
+        }
+        __syncthreads();
+
+        // phase 3: hooks for every row with entries in this tile
+        for (int i = tid; i < R; i += K2_THREADS) {
+            const int32_t mn = s_mngf[i];
+            if (mn == INF) continue;
+            const int64_t u = x0 + i;
+            const int32_t g = gf[u];
+            const int32_t pu = p[u];
+            // stochastic hooking: f_next[f[u]] <-min mngf[u]; a no-op unless
+            // mngf[u] < gf[u] because f[p[u]] <= p[p[u]] = gf[u] throughout
+            if (mn < g) atomicMin(f + pu, mn);
+            // aggressive hooking and shortcutting: f_next[u] <-min mngf[u], gf[u]
+            const int32_t m2 = mn < g ? mn : g;
+            if (m2 < pu) atomicMin(f + u, m2);
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K3: grandparents, termination count, snapshot; last CTA closes the iteration
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void close_iteration(Ctx* ctx, cudaGraphConditionalHandle cond, int use_cond) {
+    const int tid = threadIdx.x;
+    const int G = ctx->num_segs;
+    const int max_iters = ctx->max_iters;
+    int any = 0;
+    for (int s = tid; s < G; s += blockDim.x) {
+        Seg* S = ctx->segs + s;
+        if (!S->active) continue;
+        unsigned int ch = atomicExch(&S->changed, 0u);
+        int it = S->iters + 1;
+        S->iters = it;
+        if (s == 0 && it <= TRACE_LEN) ctx->sum.trace[it - 1] = ch;
+        if (ch == 0) {
+            S->active = 0;
+            S->converged = 1;
+        } else if (it >= max_iters) {
+            S->active = 0;
+            S->status |= DEV_ERR_MAX_ITERS;
+        } else {
+            any = 1;
+        }
+    }
+    any = __syncthreads_or(any);
+    if (tid == 0) {
+        ctx->k3_done = 0;
+        int li = ctx->loop_iter + 1;
+        ctx->loop_iter = li;
+        ctx->any_active = any;
+        if (use_cond) cudaGraphSetConditional(cond, (any && li < ctx->loop_limit) ? 1u : 0u);
+    }
+}
+
+__global__ void __launch_bounds__(K3_THREADS)
+    k3_grandparent(Ctx* __restrict__ ctx, cudaGraphConditionalHandle cond, int use_cond) {
+    __shared__ int s_red[K3_THREADS / 32];
+    __shared__ int s_last;
+    const int tid = threadIdx.x;
+    const int64_t T = ctx->k3_total;
+    for (int64_t t = blockIdx.x; t < T; t += gridDim.x) {
+        Seg* S = ctx->segs + ctx->k3_tile_seg[t];
+        if (!S->active) continue;
+        const int64_t n = S->n;
+        const int64_t v0 = (t - S->k3_tile0) * K3_TILE;
+        int32_t* f = S->f;
+        int32_t* p = S->p;
+        int32_t* gf = S->gf;
+        int32_t fu[K3_ITEMS];
+#pragma unroll
+        for (int q = 0; q < K3_ITEMS; ++q) {
+            int64_t v = v0 + tid + q * K3_THREADS;
+            fu[q] = v < n ? f[v] : 0;
+        }
+        int c = 0;
+#pragma unroll
+        for (int q = 0; q < K3_ITEMS; ++q) {
+            int64_t v = v0 + tid + q * K3_THREADS;
+            if (v < n) {
+                const int32_t g = f[fu[q]];
+                if (g != gf[v]) {
+                    gf[v] = g;
+                    ++c;
+                }
+                p[v] = fu[q];
+            }
+        }
+        c = __reduce_add_sync(0xffffffffu, c);
+        if ((tid & 31) == 0) s_red[tid >> 5] = c;
+        __syncthreads();
+        if (tid < 32) {
+            int x = tid < K3_THREADS / 32 ? s_red[tid] : 0;
+            x = __reduce_add_sync(0xffffffffu, x);
+            if (tid == 0 && x) atomicAdd(&S->changed, (unsigned int)x);
+        }
+        __syncthreads();
+    }
+    // the last CTA to arrive closes the iteration for every segment
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        unsigned int ticket = atomicAdd(&ctx->k3_done, 1u);
+        s_last = ticket == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    close_iteration(ctx, cond, use_cond);
+}
+
+// end of a call: per-graph iteration counts and the summary
+__global__ void k_finish(Ctx* ctx, int32_t* iters_out) {
+    __shared__ long long s_it[256];
+    __shared__ int s_st[256], s_cv[256], s_act[256];
+    const int G = ctx->num_segs;
+    long long it = 0;
+    int st = 0, cv = 1, act = 0;
+    for (int s = threadIdx.x; s < G; s += blockDim.x) {
+        const Seg& S = ctx->segs[s];
+        if (iters_out) iters_out[s] = S.iters;
+        it = max(it, (long long)S.iters);
+        st |= S.status;
+        cv &= S.converged;
+        act += S.active;
+    }
+    s_it[threadIdx.x] = it;
+    s_st[threadIdx.x] = st;
+    s_cv[threadIdx.x] = cv;
+    s_act[threadIdx.x] = act;
+    __syncthreads();
+    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+        if (threadIdx.x < off) {
+            s_it[threadIdx.x] = max(s_it[threadIdx.x], s_it[threadIdx.x + off]);
+            s_st[threadIdx.x] |= s_st[threadIdx.x + off];
+            s_cv[threadIdx.x] &= s_cv[threadIdx.x + off];
+            s_act[threadIdx.x] += s_act[threadIdx.x + off];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        ctx->sum.iterations = s_it[0];
+        ctx->sum.status = s_st[0] | ctx->val_status;
+        ctx->sum.converged = s_cv[0];
+        ctx->sum.loop_iter = ctx->loop_iter;
+        ctx->sum.num_active = s_act[0];
+    }
+}
+
+}  // namespace fsv

@@ -1,0 +1,67 @@
+// fastsv_types.cuh -- device data structures shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fsv {
+
+constexpr int32_t INF = 0x7fffffff;
+constexpr int K2_THREADS = 256;
+constexpr int K3_THREADS = 256;
+constexpr int K3_ITEMS = 8;
+constexpr int K3_TILE = K3_THREADS * K3_ITEMS;
+constexpr int TRACE_LEN = 64;
+
+// status bits written by device code
+constexpr int32_t DEV_ERR_MAX_ITERS = 1;
+constexpr int32_t DEV_ERR_BAD_ROWPTR = 2;
+constexpr int32_t DEV_ERR_BAD_COLIDX = 4;
+constexpr int32_t DEV_ERR_ASYMMETRIC = 8;
+
+struct Seg {
+    const void* rp;      // row pointers (int32 or int64 by kernel instance), n+1 entries, local offsets
+    const int32_t* ci;   // neighbour ids (local)
+    int32_t* f;          // parent vector (caller's labels buffer)
+    int32_t* p;          // snapshot of f
+    int32_t* gf;         // grandparents
+    int64_t n, m;
+    int64_t k2_tile0;    // first hooking tile of this segment in the global list
+    int64_t k3_tile0;    // first grandparent tile
+    int32_t k2_ntiles, k3_ntiles;
+    int32_t active;      // 1 while iterating
+    int32_t iters;       // iterations executed
+    int32_t status;      // DEV_ERR_* bits
+    int32_t converged;   // 1 once an iteration left gf unchanged
+    unsigned int changed;  // this iteration's changed-grandparent count
+    int32_t user;        // owner tag (pool slot id), unused by the kernels
+};
+
+struct Summary {
+    int64_t iterations;     // max over segments
+    int32_t status;         // OR over segments and validation
+    int32_t converged;      // AND over segments
+    int32_t loop_iter;      // iterations the device loop executed in this call
+    int32_t num_active;     // segments still active
+    unsigned long long trace[TRACE_LEN];  // segment 0: changed count per iteration
+};
+
+struct Ctx {
+    Seg* segs;
+    int32_t num_segs;
+    int32_t k2_tile;         // merge-path items per hooking tile
+    int64_t k2_total;        // hooking tiles over all segments
+    int64_t k3_total;        // grandparent tiles over all segments
+    int32_t* k2_tile_seg;
+    int32_t* k2_tile_row;    // merge-path start row of each hooking tile (segment-local)
+    int32_t* k3_tile_seg;
+    int32_t max_iters;
+    int32_t loop_limit;      // iterations allowed in this launch of the device loop
+    int32_t loop_iter;       // iterations executed in this launch
+    unsigned int k3_done;    // CTA ticket for the last-block epilogue
+    int32_t any_active;
+    int32_t val_status;      // validation result bits
+    Summary sum;
+};
+
+}  // namespace fsv

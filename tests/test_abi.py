@@ -1,0 +1,53 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+that include/*.h declares (host-only checks; no kernel runs without a GPU)."""
+import ctypes as C
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = []
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names += re.findall(r"^\s*[A-Za-z_][\w \*]*?\b(fastsv_\w+)\s*\(", src, re.M)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol():
+    import paper_1910_05971_gb300 as fsv
+    lib = fsv.load()
+    names = _declared()
+    assert len(names) >= 16
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_names_match_header():
+    import paper_1910_05971_gb300 as fsv
+    for n in _declared():
+        assert hasattr(fsv, n), f"binding lacks {n}"
+
+
+def test_host_only_entry_points():
+    import paper_1910_05971_gb300 as fsv
+    o = fsv.fastsv_default_options()
+    assert (o.rowptr_bits, o.mode, o.max_iters, o.use_graph, o.k2_items) == (64, 0, 4096, 1, 8)
+    assert C.sizeof(fsv.fastsv_options) == 64
+    assert C.sizeof(fsv.fastsv_stats) == 568
+    assert fsv.fastsv_status_string(fsv.FASTSV_ERR_MAX_ITERS) == "FASTSV_ERR_MAX_ITERS"
+    assert fsv.fastsv_pool_bytes(10, 20) > 0
+    # invalid handles are rejected on the host without touching a device
+    assert fsv._lib.load().fastsv_destroy(None) == fsv.FASTSV_ERR_INVALID_ARG
+    assert fsv._lib.load().fastsv_cc(None, 5, None, None, None, None) == fsv.FASTSV_ERR_INVALID_ARG
+
+
+def test_library_is_built_for_sm_103a_only():
+    from paper_1910_05971_gb300 import _build
+    assert _build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+    assert os.path.exists(_build.LIB)

@@ -1,0 +1,239 @@
+"""GPU parity tests: the CUDA path (through the C ABI) against the CPU oracle.
+
+Labels and iteration counts must match exactly (integer work: bit-exact);
+in sync mode the pointer graph after every iteration must match too.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import graphgen
+import oracle
+from gpu_util import Solver, gpu_solve, oracle_batch, per_iteration_parity, to_dev, workload
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "alg2_hand_traces.json")
+
+
+def _cases():
+    with open(GOLDEN) as fh:
+        return json.load(fh)["cases"]
+
+
+@pytest.mark.parametrize("case", _cases(), ids=lambda c: c["name"])
+def test_hand_traces(case):
+    import paper_1910_05971_gb300 as fsv
+    rp, ci = oracle.csr_from_edges(case["n"], case["edges"])
+    lab, st = gpu_solve(rp, ci)
+    assert lab.tolist() == case["labels"]
+    assert st["iterations"] == case["iterations"]
+    assert st["changed_per_iter"] == case["changed"]
+    for k, f_exp in enumerate(case["f_after"], start=1):
+        got, stk = gpu_solve(rp, ci, max_iters=k)
+        assert got.tolist() == f_exp, f"after iteration {k}"
+        expect = fsv.FASTSV_OK if case["changed"][k - 1] == 0 else fsv.FASTSV_ERR_MAX_ITERS
+        assert stk["status"] == expect
+
+
+def test_exhaustive_small_graphs():
+    import itertools
+    s = Solver()
+    try:
+        for n in range(1, 6):
+            pairs = list(itertools.combinations(range(n), 2))
+            for mask in range(1 << len(pairs)):
+                edges = [pairs[i] for i in range(len(pairs)) if mask >> i & 1]
+                rp, ci = oracle.csr_from_edges(n, edges)
+                f, it, _, ch = oracle.fastsv(rp, ci)
+                got, st = s.solve(rp, ci)
+                assert np.array_equal(got, f), (n, edges)
+                assert st["iterations"] == it and st["changed_per_iter"] == ch.tolist()
+    finally:
+        s.close()
+
+
+def _ragged_graphs():
+    """Random graphs whose (rows + entries) land just below, on and above
+    multiples of the hooking tile, plus hubs spanning many tiles."""
+    rng = np.random.default_rng(99)
+    out = []
+    for n, m_und in [(1, 0), (2, 1), (300, 200), (1000, 1500), (2047, 0), (2049, 1), (3000, 5000)]:
+        edges = {(int(rng.integers(n)), int(rng.integers(n))) for _ in range(m_und)}
+        edges = sorted({(min(u, v), max(u, v)) for u, v in edges if u != v})
+        out.append(oracle.csr_from_edges(n, edges))
+    # a hub adjacent to everything plus a sparse rest: one row spans many tiles
+    n = 9000
+    edges = [(0, i) for i in range(1, n, 2)] + [(i, i + 1) for i in range(1, n - 1, 7)]
+    out.append(oracle.csr_from_edges(n, edges))
+    out.append(graphgen.rmat(11, 8, seed=7, permute=True))
+    out.append(graphgen.grid(50, 0.55, 33, seed=5))
+    return out
+
+
+@pytest.mark.parametrize("items", [4, 8, 16])
+@pytest.mark.parametrize("bits", [32, 64])
+def test_per_iteration_parity_ragged(items, bits):
+    for rp, ci in _ragged_graphs():
+        per_iteration_parity(rp, ci, bits=bits, k2_items=items)
+
+
+def test_host_loop_mode_matches():
+    rp, ci = graphgen.rmat(13, 8, seed=2, permute=True)
+    f, it, _, ch = oracle.fastsv(rp, ci)
+    got, st = gpu_solve(rp, ci, use_graph=False)
+    assert np.array_equal(got, f) and st["iterations"] == it
+    assert st["ms_k2"] > 0 and st["ms_k3"] > 0
+
+
+def test_edge_cases():
+    import paper_1910_05971_gb300 as fsv
+    torch = pytest.importorskip("torch")
+    with fsv.FastSV() as s:
+        lab = s.cc(torch.zeros(1, dtype=torch.int64, device="cuda"), torch.zeros(0, dtype=torch.int32, device="cuda"))
+        assert lab.numel() == 0 and s.stats()["iterations"] == 0
+    rp, ci = oracle.csr_from_edges(1, [])
+    got, st = gpu_solve(rp, ci)
+    assert got.tolist() == [0] and st["iterations"] == 1
+    rp, ci = oracle.csr_from_edges(500, [])
+    got, st = gpu_solve(rp, ci)
+    assert got.tolist() == list(range(500)) and st["iterations"] == 1
+    # self-loops and duplicate entries change nothing
+    rng = np.random.default_rng(5)
+    edges = sorted({(int(a), int(b)) for a, b in zip(rng.integers(400, size=300), rng.integers(400, size=300)) if a < b})
+    noisy = edges + edges[:50] + [(i, i) for i in range(0, 400, 9)]
+    f, it, _, ch = oracle.fastsv(*oracle.csr_from_edges(400, edges))
+    got, st = gpu_solve(*oracle.csr_from_edges(400, noisy))
+    assert np.array_equal(got, f) and st["iterations"] == it and st["changed_per_iter"] == ch.tolist()
+
+
+def test_iteration_cap_reports_partial_state():
+    import paper_1910_05971_gb300 as fsv
+    n = 4000
+    rp, ci = oracle.csr_from_edges(n, [(i, i + 1) for i in range(n - 1)])
+    f2, it2, conv, _ = oracle.fastsv(rp, ci, max_iters=2)
+    assert not conv
+    got, st = gpu_solve(rp, ci, max_iters=2)
+    assert st["status"] == fsv.FASTSV_ERR_MAX_ITERS and st["iterations"] == 2
+    assert np.array_equal(got, f2)
+    with pytest.raises(fsv.FastSVError):
+        with fsv.FastSV(max_iters=2) as s:
+            s.cc(to_dev(rp), to_dev(ci))
+
+
+def test_validation_rejects_malformed_csr():
+    import paper_1910_05971_gb300 as fsv
+    rp, ci = oracle.csr_from_edges(6, [(0, 1), (1, 2), (3, 4)])
+    got, st = gpu_solve(rp, ci, validate=2)
+    assert st["status"] == fsv.FASTSV_OK
+    bad = ci.copy()
+    bad[0] = 17
+    with fsv.FastSV(validate=1) as s:
+        with pytest.raises(fsv.FastSVError) as e:
+            s.cc(to_dev(rp), to_dev(bad))
+        assert e.value.status == fsv.FASTSV_ERR_INVALID_GRAPH
+    badrp = rp.copy()
+    badrp[2], badrp[3] = badrp[3], badrp[2]
+    with fsv.FastSV(validate=1) as s:
+        with pytest.raises(fsv.FastSVError) as e:
+            s.cc(to_dev(badrp), to_dev(ci))
+        assert e.value.status == fsv.FASTSV_ERR_INVALID_GRAPH
+    rp_a, ci_a = oracle.csr_from_edges(4, [(0, 1), (2, 3)])
+    ci_a = ci_a.copy()
+    ci_a[ci_a.tolist().index(0)] = 2  # row 1 now points to 2, row 2 does not point back
+    with fsv.FastSV(validate=2) as s:
+        with pytest.raises(fsv.FastSVError) as e:
+            s.cc(to_dev(rp_a), to_dev(np.sort(ci_a)))
+        assert e.value.status == fsv.FASTSV_ERR_INVALID_GRAPH
+
+
+def test_malformed_csr_without_validation_stays_in_bounds():
+    """With validation off a malformed CSR is outside the contract, but the
+    kernels clamp every index, so the call completes and the handle stays usable."""
+    import paper_1910_05971_gb300 as fsv
+    rp, ci = oracle.csr_from_edges(6, [(0, 1), (1, 2), (3, 4)])
+    bad = ci.copy()
+    bad[0] = 1 << 30
+    with fsv.FastSV() as s:
+        s.cc(to_dev(rp), to_dev(bad), check_status=False)
+        s.stats()
+        lab = s.cc(to_dev(rp), to_dev(ci))
+        assert lab.cpu().tolist() == [0, 0, 0, 3, 3, 5]
+
+
+def test_allocation_failure_is_reported_and_recoverable():
+    import paper_1910_05971_gb300 as fsv
+    rp, ci = graphgen.rmat(10, 8, seed=4)
+    f, it, _, _ = oracle.fastsv(rp, ci)
+    with fsv.FastSV(fail_alloc_after=1) as s:
+        with pytest.raises(fsv.FastSVError) as e:
+            s.cc(to_dev(rp), to_dev(ci))
+        assert e.value.status == fsv.FASTSV_ERR_OOM
+        lab = s.cc(to_dev(rp), to_dev(ci))
+        assert np.array_equal(lab.cpu().numpy(), f)
+
+
+def test_host_buffer_entry_point():
+    import paper_1910_05971_gb300 as fsv
+    torch = pytest.importorskip("torch")
+    rp, ci = graphgen.rmat(14, 16, seed=8, permute=True)
+    f, it, _, _ = oracle.fastsv(rp, ci, form="omp")
+    rp_h = torch.from_numpy(rp).pin_memory()
+    ci_h = torch.from_numpy(ci).pin_memory()
+    with fsv.FastSV() as s:
+        lab = s.cc_host(rp_h, ci_h)
+        assert np.array_equal(lab.numpy(), f)
+        assert s.stats()["iterations"] == it
+
+
+def test_non_default_stream_and_launch_count():
+    import paper_1910_05971_gb300 as fsv
+    torch = pytest.importorskip("torch")
+    rp, ci = graphgen.rmat(12, 8, seed=6, permute=True)
+    f, it, _, _ = oracle.fastsv(rp, ci)
+    stream = torch.cuda.Stream()
+    with fsv.FastSV() as s:
+        with torch.cuda.stream(stream):
+            rp_d, ci_d = to_dev(rp), to_dev(ci)
+            lab = s.cc(rp_d, ci_d, stream=stream)
+        stream.synchronize()
+        assert np.array_equal(lab.cpu().numpy(), f)
+        # set-up (3) + finish (1) + two kernels per device-loop iteration
+        assert s.kernel_launches() == 4 + 2 * it
+
+
+# ---------------------------------------------------------------------------
+# the named workloads at full size
+# ---------------------------------------------------------------------------
+
+def test_rmat_s16_full_per_iteration():
+    rp, ci = workload("rmat_s16")
+    k = per_iteration_parity(rp, ci, bits=32)
+    f, it, _, _ = oracle.fastsv(rp, ci)
+    assert k == it
+    assert np.array_equal(f, oracle.uf(rp, ci))
+
+
+def test_grid_full():
+    rp, ci = workload("grid_4096_p055_iso1M")
+    ref = oracle.uf(rp, ci)
+    f, it, conv, ch = oracle.fastsv(rp, ci, form="omp")
+    assert conv and np.array_equal(f, ref)
+    got, st = gpu_solve(rp, ci, bits=32)
+    assert np.array_equal(got, ref)
+    assert st["iterations"] == it
+    assert st["changed_per_iter"] == ch.tolist()[:64]
+
+
+@pytest.mark.slow
+def test_rmat_s26_full():
+    rp, ci = workload("rmat_s26_perm")
+    got, st = gpu_solve(rp, ci, bits=64)
+    ref = oracle.uf(rp, ci)
+    assert np.array_equal(got, ref)
+    f, it, conv, ch = oracle.fastsv(rp, ci, form="omp")
+    assert conv and np.array_equal(f, ref)
+    assert st["iterations"] == it
+    assert st["changed_per_iter"] == ch.tolist()[:64]
