@@ -45,6 +45,8 @@ WORKLOADS = {
     "rmat_s26_perm": dict(desc="R-MAT scale 26, edge factor 16, a/b/c=.57/.19/.19, ids permuted, seed 3",
                           bits=64),
     "rmat_s16": dict(desc="R-MAT scale 16, edge factor 16, seed 1", bits=32),
+    "rmat_s25_ef8_perm": dict(desc="R-MAT scale 25, edge factor 8, ids permuted, seed 3 (profiling case)",
+                              bits=64),
     "grid_4096_p055_iso1M": dict(desc="4096x4096 lattice, p=0.55, +1M isolated, seed 2", bits=32),
 }
 METRIC = "CC |E|/s (GTEPS) + %HBM peak at R-MAT s26"

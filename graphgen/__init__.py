@@ -247,8 +247,15 @@ def rmat_s26():
     return rmat(26, 16, seed=3, permute=True)
 
 
+def rmat_s25_ef8():
+    """R-MAT scale 25, edge factor 8, ids permuted (seed 3): the profiling
+    case (its grandparent vector, 134 MB, exceeds L2; ~2.5 GB on the device)."""
+    return rmat(25, 8, seed=3, permute=True)
+
+
 WORKLOADS = {
     "rmat_s16": rmat_s16,
+    "rmat_s25_ef8_perm": rmat_s25_ef8,
     "grid_4096_p055_iso1M": grid_4096,
     "rmat_s26_perm": rmat_s26,
 }

@@ -137,8 +137,8 @@ static fastsv_status k3_grid_for(fastsv_ctx* h, int* grid) {
 }
 
 // the device-side loop: WHILE(cond) { k2_hook; k3_grandparent }
-fastsv_status get_loop_graph(fastsv_ctx* h, int rp64, int items, LoopGraph** out) {
-    GraphKey key{rp64, items, h->opt.mode};
+fastsv_status get_loop_graph(fastsv_ctx* h, Ctx* ctx, int rp64, int items, LoopGraph** out) {
+    GraphKey key{rp64, items, h->opt.mode, ctx};
     auto it = h->graphs.find(key);
     if (it != h->graphs.end()) {
         *out = &it->second;
@@ -164,7 +164,6 @@ fastsv_status get_loop_graph(fastsv_ctx* h, int rp64, int items, LoopGraph** out
     FSV_CUDA(h, cudaGraphAddNode(&cond_node, lg.graph, nullptr, nullptr, 0, &cp));
     cudaGraph_t body = cp.conditional.phGraph_out[0];
 
-    Ctx* ctx = h->d_ctx;
     cudaGraphConditionalHandle cond = lg.cond;
     int use_cond = 1;
     void* k2args[] = {(void*)&ctx, (void*)&cond, (void*)&use_cond};
@@ -191,10 +190,10 @@ fastsv_status get_loop_graph(fastsv_ctx* h, int rp64, int items, LoopGraph** out
     return FASTSV_OK;
 }
 
-fastsv_status run_loop(fastsv_ctx* h, int rp64, int items, cudaStream_t s) {
+fastsv_status run_loop(fastsv_ctx* h, Ctx* ctx, int rp64, int items, cudaStream_t s) {
     if (h->opt.use_graph) {
         LoopGraph* lg = nullptr;
-        fastsv_status st = get_loop_graph(h, rp64, items, &lg);
+        fastsv_status st = get_loop_graph(h, ctx, rp64, items, &lg);
         if (st != FASTSV_OK) return st;
         FSV_CUDA(h, cudaGraphLaunch(lg->exec, s));
         h->pending_loop_kernels = 2;
@@ -211,10 +210,9 @@ fastsv_status run_loop(fastsv_ctx* h, int rp64, int items, cudaStream_t s) {
     for (int i = 0; i < 3; ++i) FSV_CUDA(h, cudaEventCreate(&e[i]));
     float t2 = 0.f, t3 = 0.f;
     int iters = 0;
-    Ctx* ctx = h->d_ctx;
     cudaGraphConditionalHandle none = 0;
     int no_cond = 0;
-    int32_t limit = h->opt.max_iters;
+    int32_t limit = h->loop_limit_host;
     fastsv_status rc = FASTSV_OK;
     for (;;) {
         void* a2[] = {(void*)&ctx, (void*)&none, (void*)&no_cond};
@@ -237,7 +235,7 @@ fastsv_status run_loop(fastsv_ctx* h, int rp64, int items, cudaStream_t s) {
         t2 += a;
         t3 += b;
         ++iters;
-        if (*(int32_t*)h->h_scalar == 0 || iters > limit) break;
+        if (*(int32_t*)h->h_scalar == 0 || iters >= limit) break;
     }
     for (int i = 0; i < 3; ++i) cudaEventDestroy(e[i]);
     h->ms_k2 = t2;
@@ -246,7 +244,18 @@ fastsv_status run_loop(fastsv_ctx* h, int rp64, int items, cudaStream_t s) {
     return rc;
 }
 
-static int setup_grid(const fastsv_ctx* h) { return h->num_sms * 8; }
+int setup_grid(const fastsv_ctx* h) { return h->num_sms * 8; }
+
+// prefix sums of tile counts, merge-path partition, identity state of
+// segments that have not iterated yet (int32 row pointers)
+fastsv_status rebuild_tiles(fastsv_ctx* h, Ctx* ctx, cudaStream_t s) {
+    k_scan_tiles<<<1, 1024, 0, s>>>(ctx);
+    k_partition<int32_t><<<setup_grid(h), 256, 0, s>>>(ctx);
+    k_init_state<<<setup_grid(h), 256, 0, s>>>(ctx);
+    h->launches += 3;
+    FSV_CUDA(h, cudaGetLastError());
+    return FASTSV_OK;
+}
 
 // stream ordering between consecutive calls of one handle
 static void order_after_previous(fastsv_ctx* h, cudaStream_t s) {
@@ -324,7 +333,8 @@ static fastsv_status solve_single(fastsv_ctx* h, int64_t n, int64_t m, const voi
     FSV_CUDA(h, cudaGetLastError());
     if ((st = run_validation(h, rp64, s)) != FASTSV_OK) return st;
     FSV_CUDA(h, cudaEventRecord(h->ev_setup, s));
-    if ((st = run_loop(h, rp64, items, s)) != FASTSV_OK) return st;
+    h->loop_limit_host = prm.loop_limit;
+    if ((st = run_loop(h, h->d_ctx, rp64, items, s)) != FASTSV_OK) return st;
     return finish_call(h, s, nullptr, n, m, true);
 }
 
@@ -547,7 +557,8 @@ fastsv_status fastsv_cc_batched(fastsv_t h, int32_t G, const int64_t* vtx_off, c
     if ((st = run_validation(h, 0, s)) != FASTSV_OK) return st;
     FSV_CUDA(h, cudaEventRecord(h->ev_setup, s));
     if (N > 0) {
-        if ((st = run_loop(h, 0, items, s)) != FASTSV_OK) return st;
+        h->loop_limit_host = prm.loop_limit;
+        if ((st = run_loop(h, h->d_ctx, 0, items, s)) != FASTSV_OK) return st;
     } else {
         h->pending_loop_kernels = 0;
     }

@@ -15,10 +15,12 @@ struct GraphKey {
     int rp64;
     int items;
     int mode;
+    const void* ctx;
     bool operator<(const GraphKey& o) const {
         if (rp64 != o.rp64) return rp64 < o.rp64;
         if (items != o.items) return items < o.items;
-        return mode < o.mode;
+        if (mode != o.mode) return mode < o.mode;
+        return ctx < o.ctx;
     }
 };
 
@@ -81,6 +83,8 @@ struct fastsv_ctx {
     int64_t pending_fixed_launches = 0;  // set-up kernels of the pending call
     int pending_loop_kernels = 0;        // kernels per device-loop iteration of the pending call
     int alloc_count = 0;
+    int32_t loop_limit_host = 0;         // iteration cap of the host-loop mode
+    bool pool_loop_pending = false;      // a pool step's device loop whose kernels are not counted yet
 
     fsv::Pool* pool = nullptr;
 };
@@ -98,8 +102,10 @@ fastsv_status cuda_fail(fastsv_ctx* h, cudaError_t e);
 // device allocation through the handle (counts allocations for the test hook)
 fastsv_status dev_alloc(fastsv_ctx* h, void** p, size_t bytes);
 fastsv_status ensure_workspace(fastsv_ctx* h, int64_t n, int64_t k2_tiles, int64_t k3_tiles, int64_t segs);
-fastsv_status get_loop_graph(fastsv_ctx* h, int rp64, int items, LoopGraph** out);
-fastsv_status run_loop(fastsv_ctx* h, int rp64, int items, cudaStream_t s);
+fastsv_status get_loop_graph(fastsv_ctx* h, Ctx* ctx, int rp64, int items, LoopGraph** out);
+fastsv_status run_loop(fastsv_ctx* h, Ctx* ctx, int rp64, int items, cudaStream_t s);
+fastsv_status rebuild_tiles(fastsv_ctx* h, Ctx* ctx, cudaStream_t s);
+int setup_grid(const fastsv_ctx* h);
 int k2_items(const fastsv_ctx* h);
 void pool_release(fastsv_ctx* h);
 

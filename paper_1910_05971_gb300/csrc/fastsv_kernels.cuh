@@ -208,10 +208,12 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(Ctx* ctx) {
     const int b = tid * chunk, e = min(G, b + chunk);
     long long a2 = 0, a3 = 0;
     int any = 0;
+    // only active segments get tiles (a pool keeps retired slots in place)
     for (int g = b; g < e; ++g) {
+        if (!segs[g].active) continue;
         a2 += segs[g].k2_ntiles;
         a3 += segs[g].k3_ntiles;
-        any |= segs[g].active;
+        any = 1;
     }
     s2[tid] = a2;
     s3[tid] = a3;
@@ -230,6 +232,7 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(Ctx* ctx) {
     for (int g = b; g < e; ++g) {
         segs[g].k2_tile0 = o2;
         segs[g].k3_tile0 = o3;
+        if (!segs[g].active) continue;
         o2 += segs[g].k2_ntiles;
         o3 += segs[g].k3_ntiles;
     }
@@ -259,10 +262,12 @@ __global__ void k_partition(Ctx* ctx) {
 }
 
 // f = p = gf = local identity (Algorithm 2: f[u] <- u; Algorithm 3: gf = dup(f))
+// for every active segment that has not run an iteration yet
 __global__ void k_init_state(Ctx* ctx) {
     const int64_t total = ctx->k3_total;
     for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
         const Seg& S = ctx->segs[ctx->k3_tile_seg[t]];
+        if (!S.active || S.iters != 0) continue;
         int64_t v0 = (t - S.k3_tile0) * K3_TILE;
         int64_t v1 = min(v0 + K3_TILE, S.n);
         for (int64_t v = v0 + threadIdx.x; v < v1; v += blockDim.x) {

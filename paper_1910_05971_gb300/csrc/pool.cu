@@ -1,23 +1,399 @@
-// pool.cu -- serving pool (continuous batching) entry points.
+// pool.cu -- serving pool: continuous batching of independent CC queries.
+//
+// A pool owns one HBM arena (the admission budget) and a segment table with
+// one fixed entry per slot.  Admitting a graph copies its CSR from host
+// memory into an arena region and writes its slot's entry; fastsv_pool_step
+// rebuilds the merge-path tile lists over the active slots and runs the same
+// device-side FastSV loop as the batched solve (Algorithm 2 with per-graph
+// early termination, Section 3.4) for a bounded number of iterations.  A
+// slot's state (f, p, gf, iteration count) stays resident between steps, so
+// graphs admitted later join the running batch at an iteration boundary and
+// every graph follows exactly the iteration sequence it has alone.
+#include <cstring>
+#include <map>
+#include <vector>
+
 #include "fastsv_internal.h"
 
 namespace fsv {
-struct Pool {};
+
+constexpr int ADMIT_MAX = 48;
+constexpr size_t ALIGN = 256;
+
+struct AdmitDesc {
+    const int32_t* rp;
+    const int32_t* ci;
+    int32_t* f;
+    int32_t* p;
+    int32_t* gf;
+    int64_t n, m;
+    int32_t slot;
+    int32_t pad;
+};
+
+struct AdmitBatch {
+    AdmitDesc d[ADMIT_MAX];
+    int32_t count;
+    int32_t num_slots;
+    int32_t k2_tile;
+    int32_t max_iters;
+    int32_t loop_limit;
+    int32_t pad;
+};
+
+// writes the entries of newly admitted slots and the step's loop scalars
+__global__ void k_pool_admit(Ctx* ctx, Seg* segs, int32_t* k2_seg, int32_t* k2_row, int32_t* k3_seg,
+                             AdmitBatch b) {
+    const int i = threadIdx.x;
+    if (i < b.count) {
+        const AdmitDesc& a = b.d[i];
+        Seg s;
+        s.rp = a.rp;
+        s.ci = a.ci;
+        s.f = a.f;
+        s.p = a.p;
+        s.gf = a.gf;
+        s.n = a.n;
+        s.m = a.m;
+        s.k2_tile0 = 0;
+        s.k3_tile0 = 0;
+        s.k2_ntiles = (a.m > 0 && a.n > 0) ? (int32_t)((a.n + a.m + b.k2_tile - 1) / b.k2_tile) : 0;
+        s.k3_ntiles = (int32_t)((a.n + K3_TILE - 1) / K3_TILE);
+        s.active = a.n > 0;
+        s.iters = 0;
+        s.status = 0;
+        s.converged = a.n == 0;
+        s.changed = 0;
+        s.user = a.slot;
+        segs[a.slot] = s;
+    }
+    if (i == 0) {
+        ctx->segs = segs;
+        ctx->k2_tile_seg = k2_seg;
+        ctx->k2_tile_row = k2_row;
+        ctx->k3_tile_seg = k3_seg;
+        ctx->num_segs = b.num_slots;
+        ctx->k2_tile = b.k2_tile;
+        ctx->max_iters = b.max_iters;
+        ctx->loop_limit = b.loop_limit;
+        ctx->loop_iter = 0;
+        ctx->k3_done = 0;
+        ctx->val_status = 0;
+    }
+}
+
+struct Slot {
+    int state = 0;  // 0 free, 1 admitted (copies in flight), 2 iterating on the device
+    int64_t n = 0, m = 0;
+    size_t off = 0, bytes = 0;
+    int32_t* labels_host = nullptr;
+};
+
+struct Pool {
+    Ctx* d_ctx = nullptr;
+    Seg* d_segs = nullptr;
+    Seg* h_segs = nullptr;  // pinned mirror of the segment table after each step
+    int32_t* d_k2_seg = nullptr;
+    int32_t* d_k2_row = nullptr;
+    int32_t* d_k3_seg = nullptr;
+    char* arena = nullptr;
+    size_t budget = 0, used = 0;
+    std::map<size_t, size_t> free_list;  // offset -> size, coalesced
+    int max_slots = 0;
+    std::vector<Slot> slots;
+    std::vector<int> admitted;  // slots whose copies were enqueued since the last step
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t copy_done = nullptr, step_done = nullptr;
+    bool stepped = false;
+    bool dirty = false;
+};
+
+static size_t align_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
+
+static size_t region_bytes(int64_t n, int64_t m) {
+    return align_up((size_t)(n + 1) * 4) + align_up((size_t)(m > 0 ? m : 1) * 4) + 3 * align_up((size_t)n * 4);
+}
+
+static bool arena_alloc(Pool* P, size_t bytes, size_t* off) {
+    for (auto it = P->free_list.begin(); it != P->free_list.end(); ++it) {
+        if (it->second >= bytes) {
+            *off = it->first;
+            size_t rest = it->second - bytes;
+            size_t start = it->first + bytes;
+            P->free_list.erase(it);
+            if (rest) P->free_list[start] = rest;
+            P->used += bytes;
+            return true;
+        }
+    }
+    return false;
+}
+
+static void arena_free(Pool* P, size_t off, size_t bytes) {
+    P->used -= bytes;
+    auto it = P->free_list.emplace(off, bytes).first;
+    auto next = std::next(it);
+    if (next != P->free_list.end() && it->first + it->second == next->first) {
+        it->second += next->second;
+        P->free_list.erase(next);
+    }
+    if (it != P->free_list.begin()) {
+        auto prev = std::prev(it);
+        if (prev->first + prev->second == it->first) {
+            prev->second += it->second;
+            P->free_list.erase(it);
+        }
+    }
+}
+
 void pool_release(fastsv_ctx* h) {
-    delete h->pool;
+    Pool* P = h->pool;
+    if (!P) return;
+    if (P->step_done) cudaEventSynchronize(P->step_done);
+    if (P->copy_stream) cudaStreamSynchronize(P->copy_stream);
+    if (P->d_ctx) cudaFree(P->d_ctx);
+    if (P->d_segs) cudaFree(P->d_segs);
+    if (P->h_segs) cudaFreeHost(P->h_segs);
+    if (P->d_k2_seg) cudaFree(P->d_k2_seg);
+    if (P->d_k2_row) cudaFree(P->d_k2_row);
+    if (P->d_k3_seg) cudaFree(P->d_k3_seg);
+    if (P->arena) cudaFree(P->arena);
+    if (P->copy_stream) cudaStreamDestroy(P->copy_stream);
+    if (P->copy_done) cudaEventDestroy(P->copy_done);
+    if (P->step_done) cudaEventDestroy(P->step_done);
+    delete P;
     h->pool = nullptr;
 }
+
 }  // namespace fsv
 
+using namespace fsv;
+
 extern "C" {
-fastsv_status fastsv_pool_create(fastsv_t, size_t, int32_t) { return FASTSV_ERR_UNSUPPORTED; }
-size_t fastsv_pool_bytes(int64_t n, int64_t m) { return (size_t)(n + 1) * 4 + (size_t)m * 4 + (size_t)n * 12; }
-fastsv_status fastsv_pool_add(fastsv_t, int64_t, const int32_t*, const int32_t*, int32_t*, int32_t*) {
-    return FASTSV_ERR_UNSUPPORTED;
+
+size_t fastsv_pool_bytes(int64_t n, int64_t m) {
+    if (n < 0 || m < 0) return 0;
+    return region_bytes(n, m);
 }
-fastsv_status fastsv_pool_step(fastsv_t, int32_t, void*) { return FASTSV_ERR_UNSUPPORTED; }
-fastsv_status fastsv_pool_poll(fastsv_t, int32_t*, int32_t*, int32_t, int32_t*, int32_t*) {
-    return FASTSV_ERR_UNSUPPORTED;
+
+fastsv_status fastsv_pool_create(fastsv_t h, size_t budget, int32_t max_slots) {
+    if (!h || budget < ALIGN || max_slots < 1 || max_slots > (1 << 20)) return FASTSV_ERR_INVALID_ARG;
+    if (h->pool) return FASTSV_ERR_INVALID_ARG;
+    Pool* P = new Pool();
+    h->pool = P;
+    P->budget = budget / ALIGN * ALIGN;
+    P->max_slots = max_slots;
+    P->slots.resize(max_slots);
+    const int64_t tile = (int64_t)K2_THREADS * k2_items(h);
+    // every slot needs at least 4(n+m) bytes, so n + m <= budget / 4 over all slots
+    const int64_t cap2 = (int64_t)(P->budget / 4) / tile + max_slots + 1;
+    const int64_t cap3 = (int64_t)(P->budget / 16) / K3_TILE + max_slots + 1;
+    fastsv_status st = FASTSV_OK;
+    cudaError_t e = cudaSuccess;
+    if ((st = dev_alloc(h, (void**)&P->d_ctx, sizeof(Ctx))) != FASTSV_OK ||
+        (st = dev_alloc(h, (void**)&P->d_segs, sizeof(Seg) * (size_t)max_slots)) != FASTSV_OK ||
+        (st = dev_alloc(h, (void**)&P->d_k2_seg, 4 * (size_t)cap2)) != FASTSV_OK ||
+        (st = dev_alloc(h, (void**)&P->d_k2_row, 4 * (size_t)cap2)) != FASTSV_OK ||
+        (st = dev_alloc(h, (void**)&P->d_k3_seg, 4 * (size_t)cap3)) != FASTSV_OK ||
+        (st = dev_alloc(h, (void**)&P->arena, P->budget)) != FASTSV_OK) {
+        pool_release(h);
+        return st;
+    }
+    e = cudaMemset(P->d_ctx, 0, sizeof(Ctx));
+    if (e == cudaSuccess) e = cudaMemset(P->d_segs, 0, sizeof(Seg) * (size_t)max_slots);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&P->h_segs, sizeof(Seg) * (size_t)max_slots);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->copy_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->copy_done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->step_done, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        st = cuda_fail(h, e);
+        pool_release(h);
+        return st;
+    }
+    memset(P->h_segs, 0, sizeof(Seg) * (size_t)max_slots);
+    P->free_list[0] = P->budget;
+    return FASTSV_OK;
 }
-fastsv_status fastsv_pool_usage(fastsv_t, int32_t*, size_t*) { return FASTSV_ERR_UNSUPPORTED; }
+
+fastsv_status fastsv_pool_add(fastsv_t h, int64_t n, const int32_t* rp, const int32_t* ci, int32_t* labels_host,
+                              int32_t* slot_out) {
+    if (!h || !h->pool || !slot_out || n < 0 || n > (int64_t)INT32_MAX) return FASTSV_ERR_INVALID_ARG;
+    if (!rp || (n > 0 && !labels_host)) return FASTSV_ERR_INVALID_ARG;
+    Pool* P = h->pool;
+    *slot_out = -1;
+    const int64_t m = rp[n];
+    if (m < 0 || (m > 0 && !ci)) return FASTSV_ERR_INVALID_ARG;
+    const size_t bytes = region_bytes(n, m);
+    if (bytes > P->budget) return FASTSV_ERR_INVALID_ARG;  // can never fit
+    int slot = -1;
+    for (int s = 0; s < P->max_slots; ++s)
+        if (P->slots[s].state == 0) {
+            slot = s;
+            break;
+        }
+    if (slot < 0) return FASTSV_ERR_FULL;
+    size_t off = 0;
+    if (!arena_alloc(P, bytes, &off)) return FASTSV_ERR_FULL;
+    Slot& S = P->slots[slot];
+    S.state = 1;
+    S.n = n;
+    S.m = m;
+    S.off = off;
+    S.bytes = bytes;
+    S.labels_host = labels_host;
+    char* base = P->arena + off;
+    cudaError_t e = cudaMemcpyAsync(base, rp, (size_t)(n + 1) * 4, cudaMemcpyHostToDevice, P->copy_stream);
+    if (e == cudaSuccess && m > 0)
+        e = cudaMemcpyAsync(base + align_up((size_t)(n + 1) * 4), ci, (size_t)m * 4, cudaMemcpyHostToDevice,
+                            P->copy_stream);
+    if (e != cudaSuccess) {
+        arena_free(P, off, bytes);
+        S = Slot();
+        return cuda_fail(h, e);
+    }
+    P->admitted.push_back(slot);
+    *slot_out = slot;
+    return FASTSV_OK;
 }
+
+fastsv_status fastsv_pool_step(fastsv_t h, int32_t iters, void* stream) {
+    if (!h || !h->pool || iters < 1) return FASTSV_ERR_INVALID_ARG;
+    Pool* P = h->pool;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int items = k2_items(h);
+    const int32_t tile = K2_THREADS * items;
+    // the slot snapshot read below must be the previous step's final one
+    if (P->stepped) FSV_CUDA(h, cudaEventSynchronize(P->step_done));
+    size_t na = P->admitted.size();
+    if (na > 0) {
+        FSV_CUDA(h, cudaEventRecord(P->copy_done, P->copy_stream));
+        FSV_CUDA(h, cudaStreamWaitEvent(s, P->copy_done, 0));
+    }
+    size_t done = 0;
+    do {
+        AdmitBatch b;
+        memset(&b, 0, sizeof(b));
+        b.num_slots = P->max_slots;
+        b.k2_tile = tile;
+        b.max_iters = h->opt.max_iters;
+        b.loop_limit = iters;
+        while (done < na && b.count < ADMIT_MAX) {
+            int slot = P->admitted[done++];
+            Slot& S = P->slots[slot];
+            char* base = P->arena + S.off;
+            AdmitDesc& a = b.d[b.count++];
+            a.rp = (const int32_t*)base;
+            size_t o = align_up((size_t)(S.n + 1) * 4);
+            a.ci = (const int32_t*)(base + o);
+            o += align_up((size_t)(S.m > 0 ? S.m : 1) * 4);
+            a.f = (int32_t*)(base + o);
+            o += align_up((size_t)S.n * 4);
+            a.p = (int32_t*)(base + o);
+            o += align_up((size_t)S.n * 4);
+            a.gf = (int32_t*)(base + o);
+            a.n = S.n;
+            a.m = S.m;
+            a.slot = slot;
+            S.state = 2;
+        }
+        k_pool_admit<<<1, ADMIT_MAX, 0, s>>>(P->d_ctx, P->d_segs, P->d_k2_seg, P->d_k2_row, P->d_k3_seg, b);
+        h->launches += 1;
+        FSV_CUDA(h, cudaGetLastError());
+    } while (done < na);
+    if (na > 0) P->dirty = true;
+    P->admitted.clear();
+    if (P->dirty) {
+        fastsv_status st = rebuild_tiles(h, P->d_ctx, s);
+        if (st != FASTSV_OK) return st;
+        P->dirty = false;
+    }
+    // work remains if graphs were just admitted or the last step's snapshot
+    // shows a resident slot still iterating
+    bool any = na > 0;
+    for (int i = 0; i < P->max_slots && !any; ++i)
+        any = P->slots[i].state == 2 && P->h_segs[i].active;
+    if (any) {
+        h->loop_limit_host = iters;
+        const bool graph = h->opt.use_graph != 0;
+        fastsv_status st = run_loop(h, P->d_ctx, 0, items, s);
+        if (st != FASTSV_OK) return st;
+        if (graph) {
+            // the loop's iteration count is read back with the segment table
+            FSV_CUDA(h, cudaMemcpyAsync(h->h_scalar + 2, &P->d_ctx->loop_iter, sizeof(int32_t),
+                                        cudaMemcpyDeviceToHost, s));
+        }
+    }
+    FSV_CUDA(h, cudaMemcpyAsync(P->h_segs, P->d_segs, sizeof(Seg) * (size_t)P->max_slots, cudaMemcpyDeviceToHost, s));
+    FSV_CUDA(h, cudaEventRecord(P->step_done, s));
+    P->stepped = true;
+    h->pool_loop_pending = any && h->opt.use_graph;
+    return FASTSV_OK;
+}
+
+fastsv_status fastsv_pool_poll(fastsv_t h, int32_t* done_slots, int32_t* done_iters, int32_t cap, int32_t* n_done,
+                               int32_t* n_active) {
+    if (!h || !h->pool || !n_done || cap < 0 || (cap > 0 && !done_slots)) return FASTSV_ERR_INVALID_ARG;
+    Pool* P = h->pool;
+    *n_done = 0;
+    if (P->stepped) {
+        cudaError_t e = cudaEventSynchronize(P->step_done);
+        if (e != cudaSuccess) return cuda_fail(h, e);
+        if (h->pool_loop_pending) {
+            h->launches += 2 * (int64_t) * (int32_t*)(h->h_scalar + 2);
+            h->pool_loop_pending = false;
+        }
+    }
+    int nd = 0, act = 0;
+    std::vector<int> harvested;
+    for (int i = 0; i < P->max_slots; ++i) {
+        Slot& S = P->slots[i];
+        if (S.state != 2) {
+            if (S.state == 1) ++act;
+            continue;
+        }
+        const Seg& D = P->h_segs[i];
+        const bool finished = P->stepped && !D.active && (D.iters > 0 || S.n == 0);
+        if (!finished) {
+            ++act;
+            continue;
+        }
+        if (nd >= cap) {
+            ++act;
+            continue;
+        }
+        if (S.n > 0) {
+            size_t o = align_up((size_t)(S.n + 1) * 4) + align_up((size_t)(S.m > 0 ? S.m : 1) * 4);
+            cudaError_t e = cudaMemcpyAsync(S.labels_host, P->arena + S.off + o, (size_t)S.n * 4,
+                                            cudaMemcpyDeviceToHost, P->copy_stream);
+            if (e != cudaSuccess) return cuda_fail(h, e);
+        }
+        done_slots[nd] = i;
+        if (done_iters) done_iters[nd] = (D.status & DEV_ERR_MAX_ITERS) ? -D.iters : D.iters;
+        ++nd;
+        harvested.push_back(i);
+    }
+    if (!harvested.empty()) {
+        cudaError_t e = cudaStreamSynchronize(P->copy_stream);
+        if (e != cudaSuccess) return cuda_fail(h, e);
+        for (int i : harvested) {
+            Slot& S = P->slots[i];
+            arena_free(P, S.off, S.bytes);
+            S = Slot();
+        }
+    }
+    *n_done = nd;
+    if (n_active) *n_active = act;
+    return FASTSV_OK;
+}
+
+fastsv_status fastsv_pool_usage(fastsv_t h, int32_t* slots_used, size_t* bytes_used) {
+    if (!h || !h->pool) return FASTSV_ERR_INVALID_ARG;
+    Pool* P = h->pool;
+    int u = 0;
+    for (const Slot& S : P->slots) u += S.state != 0;
+    if (slots_used) *slots_used = u;
+    if (bytes_used) *bytes_used = P->used;
+    return FASTSV_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,124 @@
+"""GPU tests of the serving pool: a graph's labels and iteration count are the
+same alone and inside a continuously changing batch (tolerance 0)."""
+import numpy as np
+import pytest
+
+import graphgen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+def _graphs(count, seed=1):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        k = int(rng.integers(4))
+        if k == 0:
+            out.append(graphgen.rmat(int(rng.integers(6, 13)), int(rng.integers(8, 33)), seed=100 + i))
+        elif k == 1:
+            out.append(graphgen.grid(int(rng.integers(5, 80)), float(rng.uniform(0.4, 0.9)), 0, seed=200 + i))
+        elif k == 2:
+            out.append(oracle.csr_from_edges(int(rng.integers(1, 40)), []))
+        else:
+            n = int(rng.integers(2, 3000))
+            out.append(oracle.csr_from_edges(n, [(j, j + 1) for j in range(n - 1)]))
+    return [(rp.astype(np.int32), ci.astype(np.int32)) for rp, ci in out]
+
+
+def _alone(graphs):
+    res = []
+    for rp, ci in graphs:
+        f, it, conv, _ = oracle.fastsv(rp, ci)
+        assert conv
+        res.append((f, it))
+    return res
+
+
+def test_pool_continuous_admission_matches_alone():
+    import paper_1910_05971_gb300 as fsv
+    from paper_1910_05971_gb300.serve import PoolBackend
+    graphs = _graphs(40)
+    ref = _alone(graphs)
+    pool = PoolBackend(64 << 20, 16)
+    labels = [np.empty(max(len(rp) - 1, 1), np.int32) for rp, _ in graphs]
+    pending = list(range(len(graphs)))
+    slot_of = {}
+    done = {}
+    steps = 0
+    while len(done) < len(graphs):
+        # admit at most 3 per step so admissions interleave with running graphs
+        for _ in range(3):
+            if not pending:
+                break
+            g = pending[0]
+            slot = pool.add(graphs[g][0], graphs[g][1], labels[g])
+            if slot is None:
+                break
+            pending.pop(0)
+            slot_of[slot] = g
+        pool.step(1)
+        steps += 1
+        fin, _ = pool.poll()
+        for slot, iters in fin:
+            g = slot_of.pop(slot)
+            done[g] = iters
+        assert steps < 10000
+    for g, (f, it) in enumerate(ref):
+        n = len(graphs[g][0]) - 1
+        assert np.array_equal(labels[g][:n], f), g
+        assert done[g] == it, (g, done[g], it)
+    st, used, b = fsv.fastsv_pool_usage(pool.h)
+    assert used == 0 and b == 0
+    pool.close()
+
+
+def test_pool_budget_and_full():
+    import paper_1910_05971_gb300 as fsv
+    from paper_1910_05971_gb300.serve import PoolBackend
+    rp, ci = graphgen.rmat(12, 16, seed=3)
+    rp, ci = rp.astype(np.int32), ci.astype(np.int32)
+    need = fsv.fastsv_pool_bytes(len(rp) - 1, len(ci))
+    pool = PoolBackend(int(need * 2.5), 8)
+    labs = [np.empty(len(rp) - 1, np.int32) for _ in range(3)]
+    assert pool.add(rp, ci, labs[0]) is not None
+    assert pool.add(rp, ci, labs[1]) is not None
+    assert pool.add(rp, ci, labs[2]) is None           # budget exhausted: FULL
+    big_rp, big_ci = graphgen.rmat(14, 16, seed=3)
+    st, _ = fsv.fastsv_pool_add(pool.h, len(big_rp) - 1, big_rp.astype(np.int32).ctypes.data,
+                                big_ci.ctypes.data, labs[2].ctypes.data)
+    assert st in (fsv.FASTSV_ERR_FULL, fsv.FASTSV_ERR_INVALID_ARG)
+    f, it, _, _ = oracle.fastsv(rp, ci)
+    finished = []
+    for _ in range(100):
+        pool.step(2)
+        done, active = pool.poll()
+        finished += done
+        if len(finished) == 2:
+            break
+    assert len(finished) == 2 and all(i == it for _, i in finished)
+    assert np.array_equal(labs[0], f) and np.array_equal(labs[1], f)
+    assert pool.add(rp, ci, labs[2]) is not None       # space was returned
+    pool.close()
+
+
+def test_server_mix_equals_alone():
+    from paper_1910_05971_gb300.serve import Server
+    graphs = _graphs(60, seed=9)
+    ref = _alone(graphs)
+    with Server(hbm_budget_bytes=32 << 20, max_slots=12, iters_per_step=1) as srv:
+        futs = [srv.submit(rp, ci) for rp, ci in graphs]
+        res = [f.result(timeout=120) for f in futs]
+        summ = srv.summary()
+    for (lab, it), (f, it_ref) in zip(res, ref):
+        assert np.array_equal(lab, f) and it == it_ref
+    assert summ["completed"] == len(graphs) and summ["p99_s"] >= summ["p50_s"]
+
+
+def test_server_rejects_oversized_request():
+    from paper_1910_05971_gb300.serve import Server
+    rp, ci = graphgen.rmat(14, 16, seed=1)
+    with Server(hbm_budget_bytes=1 << 20, max_slots=4) as srv:
+        fut = srv.submit(rp, ci)
+        with pytest.raises(ValueError):
+            fut.result(timeout=10)
