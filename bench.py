@@ -178,6 +178,12 @@ def main():
     ap.add_argument("--k2-items", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--col-blocks", type=int, default=0)
+    ap.add_argument("--mode", default="single", choices=["single", "batched", "serve"],
+                    help="single: one large graph (default, the headline); batched: 4096 ER graphs in one "
+                         "launch vs per-graph launches; serve: replay of the request trace")
+    ap.add_argument("--graphs", type=int, default=4096, help="batched mode: number of graphs")
+    ap.add_argument("--requests", type=int, default=256, help="serve mode: trace prefix length")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -188,6 +194,12 @@ def main():
 
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.mode == "batched":
+        from paper_1910_05971_gb300 import benchmarks as bench_modes
+        return bench_modes.run_batched(args, rank, world, local_rank)
+    if args.mode == "serve":
+        from paper_1910_05971_gb300 import benchmarks as bench_modes
+        return bench_modes.run_serve(args, rank, world, local_rank)
 
     import torch
     import paper_1910_05971_gb300 as fsv
@@ -208,7 +220,7 @@ def main():
     labels = torch.empty(n, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
 
-    solver = fsv.FastSV(rowptr_bits=bits, k2_items=args.k2_items)
+    solver = fsv.FastSV(rowptr_bits=bits, k2_items=args.k2_items, col_blocks=args.col_blocks)
     for _ in range(args.warmup):
         solver.cc(rp_dev, ci_dev, labels)
     st = solver.stats()
@@ -244,7 +256,7 @@ def main():
     value = world * m / (ms * 1e-3) / 1e9
 
     # ---- dominant kernel: k2_hook durations from CUDA events (host-loop pass) ----
-    prof = fsv.FastSV(rowptr_bits=bits, k2_items=args.k2_items, use_graph=False)
+    prof = fsv.FastSV(rowptr_bits=bits, k2_items=args.k2_items, col_blocks=args.col_blocks, use_graph=False)
     k2_ms, k3_ms, it_sum = 0.0, 0.0, 0
     for _ in range(args.steps):
         prof.cc(rp_dev, ci_dev, labels)
@@ -269,7 +281,7 @@ def main():
         rp_h = torch.from_numpy(rp.astype(np.int64 if bits == 64 else np.int32)).pin_memory()
         ci_h = torch.from_numpy(ci).pin_memory()
         lab_h = torch.empty(n, dtype=torch.int32).pin_memory()
-        hsolver = fsv.FastSV(rowptr_bits=bits, k2_items=args.k2_items)
+        hsolver = fsv.FastSV(rowptr_bits=bits, k2_items=args.k2_items, col_blocks=args.col_blocks)
         hsolver.cc_host(rp_h, ci_h, lab_h)
         barrier()
         torch.cuda.synchronize()
@@ -325,7 +337,7 @@ def main():
                        "m_undirected": m // 2, "rowptr_bits": bits, "iterations": iterations,
                        "parallelism": f"replicas{world}" if world > 1 else "single",
                        "l2": "inputs larger than L2 (col_idx alone is 4m bytes), no flush",
-                       "k2_items": args.k2_items},
+                       "k2_items": args.k2_items, "col_blocks": st.get("col_blocks")},
             "roofline": {"bound": "hbm", "achieved": k2_gbs, "peak": peak, "unit": "GB/s",
                          "frac": k2_gbs / peak, "traffic": traffic,
                          "kernel": "k2_hook", "algorithmic_bytes_per_launch": k2_bytes,

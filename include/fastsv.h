@@ -83,7 +83,9 @@ typedef struct {
     int32_t timing;        /* 1: record device time of each call with CUDA events (default 1) */
     int32_t fail_alloc_after; /* test hook: >0 makes the N-th workspace allocation of this handle fail
                                  (returns FASTSV_ERR_OOM); 0 off */
-    int32_t reserved[6];
+    int32_t col_blocks;    /* column blocks of the hooking SpMV for one large graph: 0 = automatic
+                              (blocks once the grandparent vector outgrows L2), 1 = never, 2..16 = that many */
+    int32_t reserved[5];
 } fastsv_options;
 
 typedef struct {
@@ -97,7 +99,7 @@ typedef struct {
     float ms_k2;               /* host-loop mode only: total time of the hooking kernel */
     float ms_k3;               /* host-loop mode only: total time of the grandparent kernel */
     int32_t trace_len;         /* entries valid in changed_per_iter */
-    int32_t reserved;
+    int32_t col_blocks;        /* column blocks the last single-graph call used (1 = unblocked) */
     int64_t changed_per_iter[64]; /* single-graph calls: grandparents changed in iteration i */
 } fastsv_stats;
 

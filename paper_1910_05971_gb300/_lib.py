@@ -45,7 +45,8 @@ class fastsv_options(C.Structure):
         ("l2_persist", C.c_int32),
         ("timing", C.c_int32),
         ("fail_alloc_after", C.c_int32),
-        ("reserved", C.c_int32 * 6),
+        ("col_blocks", C.c_int32),
+        ("reserved", C.c_int32 * 5),
     ]
 
 
@@ -61,7 +62,7 @@ class fastsv_stats(C.Structure):
         ("ms_k2", C.c_float),
         ("ms_k3", C.c_float),
         ("trace_len", C.c_int32),
-        ("reserved", C.c_int32),
+        ("col_blocks", C.c_int32),
         ("changed_per_iter", C.c_int64 * 64),
     ]
 

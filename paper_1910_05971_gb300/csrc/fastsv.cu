@@ -298,18 +298,105 @@ static fastsv_status run_validation(fastsv_ctx* h, int rp64, cudaStream_t s) {
     return FASTSV_OK;
 }
 
+// number of column blocks for a graph (1 = unblocked): the grandparent
+// vector must be larger than the L2 share given to one block's slice, and the
+// graph dense enough that the extra per-block row pointers pay for themselves
+static int choose_col_blocks(const fastsv_ctx* h, int64_t n, int64_t m) {
+    int nb = h->opt.col_blocks;
+    if (m > (int64_t)INT32_MAX - 1) return 1;  // block row pointers are int32
+    if (nb == 1) return 1;
+    if (nb <= 0) {
+        const int64_t slice = 40ll << 20;  // bytes of gf per block kept in L2
+        if (4 * n <= slice || m < 8 * n) return 1;
+        nb = 1;
+        while (nb < MAX_COL_BLOCKS && 4 * n > slice * nb) nb <<= 1;
+    }
+    if (nb > MAX_COL_BLOCKS) nb = MAX_COL_BLOCKS;
+    return nb;
+}
+
+template <typename RP>
+static fastsv_status launch_block_build(fastsv_ctx* h, int items, int nb, int shift, int64_t n, cudaStream_t s) {
+    const int g = setup_grid(h);
+    const int64_t np1 = n + 1;
+    const int64_t chunks = (np1 + SCAN_CHUNK - 1) / SCAN_CHUNK;
+    int smem = items == 4 ? block_build_smem<4>(nb) : items == 16 ? block_build_smem<16>(nb) : block_build_smem<8>(nb);
+    const void* fc = items == 4 ? (const void*)k_block_count<RP, 4>
+                   : items == 16 ? (const void*)k_block_count<RP, 16> : (const void*)k_block_count<RP, 8>;
+    const void* fs = items == 4 ? (const void*)k_block_scatter<RP, 4>
+                   : items == 16 ? (const void*)k_block_scatter<RP, 16> : (const void*)k_block_scatter<RP, 8>;
+    FSV_CUDA(h, cudaFuncSetAttribute(fc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    FSV_CUDA(h, cudaFuncSetAttribute(fs, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    Ctx* ctx = h->d_ctx;
+    FSV_CUDA(h, cudaMemsetAsync(h->d_counts, 0, (size_t)nb * np1 * 4, s));
+    {
+        void* a[] = {(void*)&ctx, (void*)&h->d_counts, (void*)&nb, (void*)&shift};
+        FSV_CUDA(h, cudaLaunchKernel(fc, dim3(g), dim3(K2_THREADS), a, (size_t)smem, s));
+    }
+    int ch = (int)chunks;
+    k_scan_chunk_sums<<<(unsigned)(nb * chunks), SCAN_THREADS, 0, s>>>(h->d_counts, np1, ch, h->d_sums);
+    k_scan_sums<<<nb, 1024, 0, s>>>(h->d_sums, ch);
+    k_scan_apply<<<(unsigned)(nb * chunks), SCAN_THREADS, 0, s>>>(h->d_counts, h->d_rpB, np1, ch, h->d_sums);
+    FSV_CUDA(h, cudaMemsetAsync(h->d_counts, 0, (size_t)nb * np1 * 4, s));
+    {
+        void* a[] = {(void*)&ctx, (void*)&h->d_rpB, (void*)&h->d_counts, (void*)&h->d_colB, (void*)&nb,
+                     (void*)&shift};
+        FSV_CUDA(h, cudaLaunchKernel(fs, dim3(g), dim3(K2_THREADS), a, (size_t)smem, s));
+    }
+    h->pending_fixed_launches += 5;
+    FSV_CUDA(h, cudaGetLastError());
+    return FASTSV_OK;
+}
+
+static fastsv_status ensure_block_workspace(fastsv_ctx* h, int nb, int64_t n, int64_t m) {
+    const int64_t cells = (int64_t)nb * (n + 1);
+    const int64_t sums = (int64_t)nb * ((n + 1 + SCAN_CHUNK - 1) / SCAN_CHUNK) + 1;
+    fastsv_status st;
+    if (cells > h->cap_blk) {
+        dev_free((void**)&h->d_counts);
+        dev_free((void**)&h->d_rpB);
+        h->cap_blk = 0;
+        if ((st = dev_alloc(h, (void**)&h->d_counts, (size_t)cells * 4)) != FASTSV_OK) return st;
+        if ((st = dev_alloc(h, (void**)&h->d_rpB, (size_t)cells * 4)) != FASTSV_OK) {
+            dev_free((void**)&h->d_counts);
+            return st;
+        }
+        h->cap_blk = cells;
+    }
+    if (sums > h->cap_sums) {
+        dev_free((void**)&h->d_sums);
+        h->cap_sums = 0;
+        if ((st = dev_alloc(h, (void**)&h->d_sums, (size_t)sums * 4)) != FASTSV_OK) return st;
+        h->cap_sums = sums;
+    }
+    if (m > h->cap_colB) {
+        dev_free((void**)&h->d_colB);
+        h->cap_colB = 0;
+        if ((st = dev_alloc(h, (void**)&h->d_colB, (size_t)m * 4)) != FASTSV_OK) return st;
+        h->cap_colB = m;
+    }
+    return FASTSV_OK;
+}
+
 static fastsv_status solve_single(fastsv_ctx* h, int64_t n, int64_t m, const void* rp, const int32_t* ci,
                                   int32_t* labels, cudaStream_t s) {
     const int rp64 = h->opt.rowptr_bits == 64;
     const int items = k2_items(h);
     const int64_t tile = (int64_t)K2_THREADS * items;
+    const int nb = m > 0 ? choose_col_blocks(h, n, m) : 1;
+    int shift = 0;
+    while (shift < 31 && ((int64_t)nb << shift) < n) ++shift;
+    const int nb_eff = nb > 1 ? (int)((n + (1ll << shift) - 1) >> shift) : 1;
     const int64_t t2 = m > 0 ? (n + m + tile - 1) / tile : 0;
+    const int64_t t2b = nb_eff > 1 ? ((int64_t)nb_eff * n + m) / tile + nb_eff + 1 : 0;
     const int64_t t3 = (n + K3_TILE - 1) / K3_TILE;
-    if (t2 > INT32_MAX || t3 > INT32_MAX) return FASTSV_ERR_UNSUPPORTED;
-    fastsv_status st = ensure_workspace(h, n, t2, t3, 1);
+    if (t2 > INT32_MAX || t2b > INT32_MAX || t3 > INT32_MAX) return FASTSV_ERR_UNSUPPORTED;
+    fastsv_status st = ensure_workspace(h, n, t2 > t2b ? t2 : t2b, t3, 1 + nb_eff);
     if (st != FASTSV_OK) return st;
+    if (nb_eff > 1 && (st = ensure_block_workspace(h, nb_eff, n, m)) != FASTSV_OK) return st;
     h->pending_fixed_launches = 0;
     h->ms_k2 = h->ms_k3 = 0.f;
+    h->last_col_blocks = nb_eff;
     FSV_CUDA(h, cudaEventRecord(h->ev_start, s));
     SingleParams prm;
     prm.rp = rp;
@@ -328,13 +415,27 @@ static fastsv_status solve_single(fastsv_ctx* h, int64_t n, int64_t m, const voi
         k_partition<int64_t><<<setup_grid(h), 256, 0, s>>>(h->d_ctx);
     else
         k_partition<int32_t><<<setup_grid(h), 256, 0, s>>>(h->d_ctx);
-    k_init_state<<<setup_grid(h), 256, 0, s>>>(h->d_ctx);
-    h->pending_fixed_launches += 3;
+    h->pending_fixed_launches += 2;
     FSV_CUDA(h, cudaGetLastError());
     if ((st = run_validation(h, rp64, s)) != FASTSV_OK) return st;
+    int loop_rp64 = rp64;
+    if (nb_eff > 1) {
+        // split the columns into blocks, then partition every block's CSR
+        st = rp64 ? launch_block_build<int64_t>(h, items, nb_eff, shift, n, s)
+                  : launch_block_build<int32_t>(h, items, nb_eff, shift, n, s);
+        if (st != FASTSV_OK) return st;
+        k_setup_blocks<<<1, 1, 0, s>>>(h->d_ctx, h->d_rpB, h->d_colB, nb_eff, (int32_t)tile);
+        k_scan_tiles<<<1, 1024, 0, s>>>(h->d_ctx);
+        k_partition<int32_t><<<setup_grid(h), 256, 0, s>>>(h->d_ctx);
+        h->pending_fixed_launches += 3;
+        loop_rp64 = 0;
+    }
+    k_init_state<<<setup_grid(h), 256, 0, s>>>(h->d_ctx);
+    h->pending_fixed_launches += 1;
+    FSV_CUDA(h, cudaGetLastError());
     FSV_CUDA(h, cudaEventRecord(h->ev_setup, s));
     h->loop_limit_host = prm.loop_limit;
-    if ((st = run_loop(h, h->d_ctx, rp64, items, s)) != FASTSV_OK) return st;
+    if ((st = run_loop(h, h->d_ctx, loop_rp64, items, s)) != FASTSV_OK) return st;
     return finish_call(h, s, nullptr, n, m, true);
 }
 
@@ -426,6 +527,10 @@ fastsv_status fastsv_destroy(fastsv_t h) {
     dev_free((void**)&h->d_k3_seg);
     dev_free((void**)&h->d_p);
     dev_free((void**)&h->d_gf);
+    dev_free((void**)&h->d_counts);
+    dev_free((void**)&h->d_rpB);
+    dev_free((void**)&h->d_sums);
+    dev_free((void**)&h->d_colB);
     dev_free(&h->d_rp_copy);
     dev_free((void**)&h->d_ci_copy);
     dev_free((void**)&h->d_lab_copy);
@@ -608,6 +713,7 @@ fastsv_status fastsv_get_stats(fastsv_t h, fastsv_stats* out) {
     out->ms_k3 = h->ms_k3;
     int len = (int)(S.iterations < TRACE_LEN ? S.iterations : TRACE_LEN);
     out->trace_len = h->single ? len : 0;
+    out->col_blocks = h->single ? h->last_col_blocks : 1;
     for (int i = 0; i < out->trace_len; ++i) out->changed_per_iter[i] = (int64_t)S.trace[i];
     return (fastsv_status)h->last_status;
 }

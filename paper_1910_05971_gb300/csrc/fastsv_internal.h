@@ -53,6 +53,16 @@ struct fastsv_ctx {
     int32_t* d_gf = nullptr;
     int64_t cap_n = 0;
 
+    // column-blocked copy of a large graph (see k_block_count)
+    int32_t* d_counts = nullptr;
+    int32_t* d_rpB = nullptr;
+    int64_t cap_blk = 0;
+    int32_t* d_sums = nullptr;
+    int64_t cap_sums = 0;
+    int32_t* d_colB = nullptr;
+    int64_t cap_colB = 0;
+    int last_col_blocks = 1;
+
     // device copies for the host-buffer entry point
     void* d_rp_copy = nullptr;
     size_t cap_rp_copy = 0;

@@ -127,6 +127,8 @@ __global__ void k_setup_single(Ctx* ctx, SingleParams prm, WsPtrs ws) {
     s.converged = 0;
     s.changed = 0;
     s.user = 0;
+    s.leader = 0;
+    s.pad = 0;
     ws.segs[0] = s;
     ctx->num_segs = 1;
     ctx->k2_tile = prm.k2_tile;
@@ -181,6 +183,8 @@ __global__ void k_setup_batched(Ctx* ctx, BatchParams prm, WsPtrs ws) {
         s.converged = n == 0;
         s.changed = 0;
         s.user = (int32_t)g;
+        s.leader = (int32_t)g;
+        s.pad = 0;
         ws.segs[g] = s;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -326,6 +330,270 @@ __global__ void k_validate(Ctx* ctx, int check_sym) {
 }
 
 // ---------------------------------------------------------------------------
+// Column blocking of one graph (set-up, once per call)
+//
+// Hooking gathers gf[col_idx[e]] at random positions.  When gf is larger
+// than L2 most gathers miss.  Splitting the columns into nb ranges of 2^shift
+// ids and running one hooking pass per range keeps every pass's gathers
+// inside an L2-resident slice of gf.  A row's minimum over all its entries is
+// the minimum of its per-range minima and every hook is a min, so hooking
+// with each range's minimum gives exactly the f of the unsplit SpMV.  (This
+// is the single-GPU counterpart of the 2-D distribution of A in Section 4.2,
+// where each process column owns a range of columns.)
+//
+// Layout: counts / rpB are nb rows of n+1 int32 (block-major), colB holds
+// the entries of block 0, then block 1, ... each as a CSR over all n rows.
+// ---------------------------------------------------------------------------
+
+constexpr int MAX_COL_BLOCKS = 16;
+
+__device__ __forceinline__ int col_block(int32_t c, int shift, int nb) {
+    int b = (int)((uint32_t)c >> shift);
+    return b < nb ? b : nb - 1;
+}
+
+template <int ITEMS>
+constexpr int block_build_smem(int nb) {
+    return (3 * (K2_THREADS * ITEMS + 1) + (K2_THREADS * ITEMS + 1) * nb) * (int)sizeof(int32_t);
+}
+
+// Loads the tile's row ends and column ids (coalesced) into shared memory and
+// walks the merge path; fn(row_local, entry_local) is called once per entry.
+template <typename RP, int ITEMS, typename Fn>
+__device__ __forceinline__ void tile_walk(const int32_t* s_rowend, int nfull, int E, int D, Fn fn) {
+    const int k0 = threadIdx.x * ITEMS;
+    if (k0 >= D) return;
+    int lo = 0, hi = nfull;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (s_rowend[mid] + mid < k0)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    int r = lo, y = k0 - lo;
+    const int kend = min(k0 + ITEMS, D);
+    for (int k = k0; k < kend; ++k) {
+        if (r < nfull && y >= s_rowend[r]) {
+            ++r;
+        } else {
+            if (y < E) fn(r, y);
+            ++y;
+        }
+    }
+}
+
+// per tile of the graph's own merge-path partition (segment 0): row ends,
+// column ids, row count R, entry count E; returns false for an empty tile
+template <typename RP>
+__device__ __forceinline__ bool load_tile(const Seg& S, int64_t t, int64_t tile, const int32_t* tile_row,
+                                          int32_t* s_rowend, int32_t* s_col, int64_t& x0, int& nfull, int& R,
+                                          int& E, int& D) {
+    const RP* rp = (const RP*)S.rp;
+    const int64_t n = S.n, m = S.m;
+    const int64_t lt = t - S.k2_tile0;
+    const int64_t d0 = lt * tile, d1 = min(d0 + tile, n + m);
+    x0 = tile_row[t];
+    const int64_t x1 = (lt + 1 < S.k2_ntiles) ? (int64_t)tile_row[t + 1] : n;
+    if (x1 < x0) return false;
+    const int64_t y0 = d0 - x0, y1 = d1 - x1;
+    nfull = (int)(x1 - x0);
+    R = nfull + (x1 < n ? 1 : 0);
+    E = (int)(y1 - y0);
+    D = (int)(d1 - d0);
+    for (int i = threadIdx.x; i < R; i += blockDim.x) {
+        int64_t e = rp_at(rp, x0 + i + 1);
+        e = e < y1 ? e : y1;
+        e -= y0;
+        s_rowend[i] = (int32_t)(e < 0 ? 0 : e);
+    }
+    for (int j = threadIdx.x; j < E; j += blockDim.x) s_col[j] = ld_stream(S.ci + y0 + j);
+    return true;
+}
+
+// counts[b][u] = entries of row u whose column lies in block b
+template <typename RP, int ITEMS>
+__global__ void __launch_bounds__(K2_THREADS) k_block_count(Ctx* ctx, int32_t* counts, int nb, int shift) {
+    constexpr int TILE = K2_THREADS * ITEMS;
+    extern __shared__ int32_t smem[];
+    int32_t* s_rowend = smem;
+    int32_t* s_col = smem + (TILE + 1);
+    int32_t* s_cnt = smem + 3 * (TILE + 1);
+    const Seg S = ctx->segs[0];
+    const int64_t np1 = S.n + 1;
+    for (int64_t t = blockIdx.x; t < S.k2_ntiles; t += gridDim.x) {
+        int64_t x0;
+        int nfull, R, E, D;
+        if (!load_tile<RP>(S, t, TILE, ctx->k2_tile_row, s_rowend, s_col, x0, nfull, R, E, D)) continue;
+        for (int i = threadIdx.x; i < R * nb; i += blockDim.x) s_cnt[i] = 0;
+        __syncthreads();
+        tile_walk<RP, ITEMS>(s_rowend, nfull, E, D, [&](int r, int y) {
+            atomicAdd(&s_cnt[r * nb + col_block(s_col[y], shift, nb)], 1);
+        });
+        __syncthreads();
+        for (int i = threadIdx.x; i < R * nb; i += blockDim.x) {
+            const int c = s_cnt[i];
+            if (c) atomicAdd(&counts[(int64_t)(i % nb) * np1 + x0 + i / nb], c);
+        }
+        __syncthreads();
+    }
+}
+
+// colB[rpB[b][u] + k] for the k-th entry of row u in block b (order within a
+// row's block is arbitrary: the hooks only take minima)
+template <typename RP, int ITEMS>
+__global__ void __launch_bounds__(K2_THREADS)
+    k_block_scatter(Ctx* ctx, const int32_t* rpB, int32_t* cursor, int32_t* colB, int nb, int shift) {
+    constexpr int TILE = K2_THREADS * ITEMS;
+    extern __shared__ int32_t smem[];
+    int32_t* s_rowend = smem;
+    int32_t* s_col = smem + (TILE + 1);
+    int32_t* s_rank = smem + 2 * (TILE + 1);
+    int32_t* s_cnt = smem + 3 * (TILE + 1);
+    const Seg S = ctx->segs[0];
+    const int64_t np1 = S.n + 1;
+    const int64_t m = S.m;
+    for (int64_t t = blockIdx.x; t < S.k2_ntiles; t += gridDim.x) {
+        int64_t x0;
+        int nfull, R, E, D;
+        if (!load_tile<RP>(S, t, TILE, ctx->k2_tile_row, s_rowend, s_col, x0, nfull, R, E, D)) continue;
+        for (int i = threadIdx.x; i < R * nb; i += blockDim.x) s_cnt[i] = 0;
+        __syncthreads();
+        // rank of every entry among the tile's entries of the same (row, block)
+        tile_walk<RP, ITEMS>(s_rowend, nfull, E, D, [&](int r, int y) {
+            const int b = col_block(s_col[y], shift, nb);
+            const int k = atomicAdd(&s_cnt[r * nb + b], 1);
+            s_rank[y] = (k << 4) | b;  // nb <= 16
+        });
+        __syncthreads();
+        // reserve each (row, block) run of this tile in the row's block segment
+        for (int i = threadIdx.x; i < R * nb; i += blockDim.x) {
+            const int c = s_cnt[i];
+            if (c) s_cnt[i] = atomicAdd(&cursor[(int64_t)(i % nb) * np1 + x0 + i / nb], c);
+        }
+        __syncthreads();
+        tile_walk<RP, ITEMS>(s_rowend, nfull, E, D, [&](int r, int y) {
+            const int b = s_rank[y] & 15;
+            const int64_t u = x0 + r;
+            const int64_t pos = (int64_t)rpB[(int64_t)b * np1 + u] + s_cnt[r * nb + b] + (s_rank[y] >> 4);
+            if (pos >= 0 && pos < m) colB[pos] = s_col[y];
+        });
+        __syncthreads();
+    }
+}
+
+// exclusive scan of nb segments of L = n+1 int32 each (block-major), in
+// chunks of SCAN_CHUNK: chunk sums, per-segment scan of the sums, apply
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_ITEMS = 16;
+constexpr int SCAN_CHUNK = SCAN_THREADS * SCAN_ITEMS;
+
+__device__ __forceinline__ int block_exclusive_scan(int v, int* s_warp, int* total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int s = lane < (int)(blockDim.x >> 5) ? s_warp[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < (int)(blockDim.x >> 5)) s_warp[lane] = s;
+    }
+    __syncthreads();
+    const int before = (w > 0 ? s_warp[w - 1] : 0) + x - v;
+    if (total) *total = s_warp[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return before;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_chunk_sums(const int32_t* in, int64_t L, int chunks,
+                                                                 int32_t* sums) {
+    __shared__ int s_warp[32];
+    const int seg = blockIdx.x / chunks, c = blockIdx.x % chunks;
+    const int32_t* p = in + (int64_t)seg * L;
+    const int64_t base = (int64_t)c * SCAN_CHUNK;
+    int acc = 0;
+    for (int i = threadIdx.x; i < SCAN_CHUNK; i += SCAN_THREADS) {
+        int64_t j = base + i;
+        if (j < L) acc += p[j];
+    }
+    int total = 0;
+    block_exclusive_scan(acc, s_warp, &total);
+    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_sums(int32_t* sums, int chunks) {
+    __shared__ int s_warp[32];
+    int32_t* p = sums + (int64_t)blockIdx.x * chunks;  // one CTA per segment
+    int carry = 0;
+    for (int base = 0; base < chunks; base += 1024) {
+        int i = base + threadIdx.x;
+        int v = i < chunks ? p[i] : 0;
+        int total = 0;
+        int ex = block_exclusive_scan(v, s_warp, &total);
+        if (i < chunks) p[i] = carry + ex;
+        carry += total;
+    }
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_apply(const int32_t* in, int32_t* out, int64_t L, int chunks,
+                                                            const int32_t* sums) {
+    __shared__ int s_warp[32];
+    const int seg = blockIdx.x / chunks, c = blockIdx.x % chunks;
+    const int32_t* p = in + (int64_t)seg * L;
+    int32_t* q = out + (int64_t)seg * L;
+    const int64_t base = (int64_t)c * SCAN_CHUNK + (int64_t)threadIdx.x * SCAN_ITEMS;
+    int v[SCAN_ITEMS];
+    int acc = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        int64_t j = base + k;
+        v[k] = j < L ? p[j] : 0;
+        acc += v[k];
+    }
+    int run = sums[blockIdx.x] + block_exclusive_scan(acc, s_warp, nullptr);
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        int64_t j = base + k;
+        if (j < L) q[j] = run;
+        run += v[k];
+    }
+}
+
+// segments 1..nb: the column blocks of graph 0, which keeps only its
+// grandparent tiles; block b's rows are rpB[b] over colB + (entries before b)
+__global__ void k_setup_blocks(Ctx* ctx, const int32_t* rpB, const int32_t* colB, int nb, int32_t k2_tile) {
+    Seg* segs = ctx->segs;
+    const Seg g = segs[0];
+    const int64_t np1 = g.n + 1;
+    int64_t base = 0;
+    for (int b = 0; b < nb; ++b) {
+        const int64_t mb = rpB[(int64_t)b * np1 + g.n];
+        Seg s = g;
+        s.rp = rpB + (int64_t)b * np1;
+        s.ci = colB + base;
+        s.m = mb;
+        s.k2_ntiles = mb > 0 ? (int32_t)((g.n + mb + k2_tile - 1) / k2_tile) : 0;
+        s.k3_ntiles = 0;
+        s.active = 1;
+        s.leader = 0;
+        s.user = b;
+        segs[1 + b] = s;
+        base += mb;
+    }
+    segs[0].k2_ntiles = 0;
+    ctx->num_segs = nb + 1;
+}
+
+// ---------------------------------------------------------------------------
 // K2: SpMV (select2nd, min) fused with the three hooks
 // ---------------------------------------------------------------------------
 
@@ -354,7 +622,7 @@ __global__ void __launch_bounds__(K2_THREADS)
 
     for (int64_t t = blockIdx.x; t < T; t += gridDim.x) {
         const Seg* S = segs + tile_seg[t];
-        if (!S->active) continue;
+        if (!segs[S->leader].active) continue;
         const RP* __restrict__ rp = (const RP*)S->rp;
         const int32_t* __restrict__ ci = S->ci;
         const int32_t* __restrict__ gf = S->gf;
@@ -454,7 +722,7 @@ __device__ __forceinline__ void close_iteration(Ctx* ctx, cudaGraphConditionalHa
     int any = 0;
     for (int s = tid; s < G; s += blockDim.x) {
         Seg* S = ctx->segs + s;
-        if (!S->active) continue;
+        if (!S->active || S->leader != s) continue;  // column blocks follow their graph
         unsigned int ch = atomicExch(&S->changed, 0u);
         int it = S->iters + 1;
         S->iters = it;
@@ -544,6 +812,7 @@ __global__ void k_finish(Ctx* ctx, int32_t* iters_out) {
     int st = 0, cv = 1, act = 0;
     for (int s = threadIdx.x; s < G; s += blockDim.x) {
         const Seg& S = ctx->segs[s];
+        if (S.leader != s) continue;  // column blocks carry no state of their own
         if (iters_out) iters_out[s] = S.iters;
         it = max(it, (long long)S.iters);
         st |= S.status;

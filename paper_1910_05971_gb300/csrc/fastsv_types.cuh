@@ -35,6 +35,9 @@ struct Seg {
     int32_t converged;   // 1 once an iteration left gf unchanged
     unsigned int changed;  // this iteration's changed-grandparent count
     int32_t user;        // owner tag (pool slot id), unused by the kernels
+    int32_t leader;      // segment whose state governs this one: itself, or for a
+                         // column block of a graph, the graph's own segment
+    int32_t pad;
 };
 
 struct Summary {

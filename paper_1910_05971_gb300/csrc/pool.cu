@@ -65,6 +65,8 @@ __global__ void k_pool_admit(Ctx* ctx, Seg* segs, int32_t* k2_seg, int32_t* k2_r
         s.converged = a.n == 0;
         s.changed = 0;
         s.user = a.slot;
+        s.leader = a.slot;
+        s.pad = 0;
         segs[a.slot] = s;
     }
     if (i == 0) {

@@ -80,6 +80,30 @@ def test_per_iteration_parity_ragged(items, bits):
         per_iteration_parity(rp, ci, bits=bits, k2_items=items)
 
 
+@pytest.mark.parametrize("col_blocks", [2, 3, 4, 16])
+def test_per_iteration_parity_column_blocks(col_blocks):
+    """Column-blocked hooking (one pass per column range, partial minima
+    hooked directly) reproduces Algorithm 2 iteration by iteration."""
+    for bits in (32, 64):
+        for items in (4, 8):
+            for rp, ci in _ragged_graphs():
+                per_iteration_parity(rp, ci, bits=bits, k2_items=items, col_blocks=col_blocks)
+
+
+def test_column_blocks_with_unsorted_rows():
+    """Rows need not be sorted: shuffle every row and compare."""
+    rng = np.random.default_rng(4)
+    rp, ci = graphgen.rmat(12, 16, seed=9, permute=True)
+    ci = ci.copy()
+    for u in range(len(rp) - 1):
+        seg = ci[rp[u]:rp[u + 1]]
+        rng.shuffle(seg)
+    f, it, _, ch = oracle.fastsv(rp, ci)
+    for nb in (1, 4, 8):
+        got, st = gpu_solve(rp, ci, col_blocks=nb)
+        assert np.array_equal(got, f) and st["iterations"] == it and st["changed_per_iter"] == ch.tolist()
+
+
 def test_host_loop_mode_matches():
     rp, ci = graphgen.rmat(13, 8, seed=2, permute=True)
     f, it, _, ch = oracle.fastsv(rp, ci)
