@@ -83,9 +83,14 @@ typedef struct {
     int32_t timing;        /* 1: record device time of each call with CUDA events (default 1) */
     int32_t fail_alloc_after; /* test hook: >0 makes the N-th workspace allocation of this handle fail
                                  (returns FASTSV_ERR_OOM); 0 off */
-    int32_t col_blocks;    /* column blocks of the hooking SpMV for one large graph: 0 = automatic
-                              (blocks once the grandparent vector outgrows L2), 1 = never, 2..16 = that many */
-    int32_t reserved[5];
+    int32_t col_blocks;    /* column blocks of the SpMV for one large graph: 0 = automatic (currently: none)
+                              1 = never, 2..16 = that many (each call then copies the CSR once into
+                              column-block order; worth it only for graphs needing many iterations) */
+    int32_t k2_threads;    /* threads per CTA of the SpMV kernel: 64 (default) or 256 */
+    int32_t sparse_div;    /* single-graph calls: an iteration pushes from the vertices whose grandparent
+                              changed (SpMSpV, Section 4.2) instead of a full SpMV when the degree sum of
+                              those vertices is at most m / sparse_div (default 2); 0 = always full SpMV */
+    int32_t reserved[3];
 } fastsv_options;
 
 typedef struct {
@@ -96,8 +101,12 @@ typedef struct {
     int32_t converged;         /* 1 if every graph reached an unchanged f[f] */
     float ms_total;            /* device time of the last call's work on its stream (timing = 1) */
     float ms_setup;            /* of which: partitioning, state initialisation, validation */
-    float ms_k2;               /* host-loop mode only: total time of the hooking kernel */
+    float ms_k2;               /* host-loop mode only: total time of the full-SpMV kernel */
     float ms_k3;               /* host-loop mode only: total time of the grandparent kernel */
+    float ms_push;             /* host-loop mode only: total time of the sparse (push) iterations' SpMSpV */
+    float ms_hook;             /* host-loop mode only: total time of the hooking kernel */
+    int32_t sparse_iters;      /* single-graph calls: iterations that pushed from the changed vertices */
+    int32_t dense_iters;       /* iterations that ran the full SpMV */
     int32_t trace_len;         /* entries valid in changed_per_iter */
     int32_t col_blocks;        /* column blocks the last single-graph call used (1 = unblocked) */
     int64_t changed_per_iter[64]; /* single-graph calls: grandparents changed in iteration i */

@@ -43,7 +43,8 @@ def _stream_ptr(stream) -> int:
 
 def stats_dict(s: fastsv_stats) -> dict:
     return dict(n=s.n, m=s.m, iterations=s.iterations, status=s.status, converged=bool(s.converged),
-                ms_total=s.ms_total, ms_setup=s.ms_setup, ms_k2=s.ms_k2, ms_k3=s.ms_k3,
+                ms_total=s.ms_total, ms_setup=s.ms_setup, ms_k2=s.ms_k2, ms_k3=s.ms_k3, ms_push=s.ms_push,
+                ms_hook=s.ms_hook, sparse_iters=s.sparse_iters, dense_iters=s.dense_iters,
                 col_blocks=s.col_blocks, changed_per_iter=[int(s.changed_per_iter[i]) for i in range(s.trace_len)])
 
 
@@ -52,7 +53,8 @@ class FastSV:
 
     def __init__(self, rowptr_bits: int = 64, mode: int = FASTSV_MODE_SYNC, max_iters: int = 4096,
                  validate: int = 0, use_graph: bool = True, k2_items: int = 8, grid_ctas_per_sm: int = 0,
-                 l2_persist: bool = False, timing: bool = True, fail_alloc_after: int = 0, col_blocks: int = 0):
+                 l2_persist: bool = False, timing: bool = True, fail_alloc_after: int = 0, col_blocks: int = 0,
+                 k2_threads: int = 64, sparse_div: int = 2):
         _torch()
         o = fastsv_default_options()
         o.rowptr_bits = rowptr_bits
@@ -66,6 +68,8 @@ class FastSV:
         o.timing = int(timing)
         o.fail_alloc_after = fail_alloc_after
         o.col_blocks = col_blocks
+        o.k2_threads = k2_threads
+        o.sparse_div = sparse_div
         self.options = o
         self.h = fastsv_create(o)
 

@@ -46,7 +46,9 @@ class fastsv_options(C.Structure):
         ("timing", C.c_int32),
         ("fail_alloc_after", C.c_int32),
         ("col_blocks", C.c_int32),
-        ("reserved", C.c_int32 * 5),
+        ("k2_threads", C.c_int32),
+        ("sparse_div", C.c_int32),
+        ("reserved", C.c_int32 * 3),
     ]
 
 
@@ -61,6 +63,10 @@ class fastsv_stats(C.Structure):
         ("ms_setup", C.c_float),
         ("ms_k2", C.c_float),
         ("ms_k3", C.c_float),
+        ("ms_push", C.c_float),
+        ("ms_hook", C.c_float),
+        ("sparse_iters", C.c_int32),
+        ("dense_iters", C.c_int32),
         ("trace_len", C.c_int32),
         ("col_blocks", C.c_int32),
         ("changed_per_iter", C.c_int64 * 64),

@@ -14,6 +14,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <climits>
+#include <vector>
 
 #include "fastsv_internal.h"
 #include "fastsv_kernels.cuh"
@@ -79,14 +80,15 @@ fastsv_status ensure_workspace(fastsv_ctx* h, int64_t n, int64_t k2, int64_t k3,
         h->cap_k3 = c;
     }
     if (n > h->cap_n) {
-        dev_free((void**)&h->d_p);
-        dev_free((void**)&h->d_gf);
+        int32_t** arrays[4] = {&h->d_p, &h->d_gf, &h->d_mngf, &h->d_frontier};
+        for (auto a : arrays) dev_free((void**)a);
         h->cap_n = 0;
         int64_t c = n;
-        if ((st = dev_alloc(h, (void**)&h->d_p, (size_t)c * 4)) != FASTSV_OK) return st;
-        if ((st = dev_alloc(h, (void**)&h->d_gf, (size_t)c * 4)) != FASTSV_OK) {
-            dev_free((void**)&h->d_p);
-            return st;
+        for (auto a : arrays) {
+            if ((st = dev_alloc(h, (void**)a, (size_t)c * 4)) != FASTSV_OK) {
+                for (auto b : arrays) dev_free((void**)b);
+                return st;
+            }
         }
         h->cap_n = c;
     }
@@ -98,56 +100,89 @@ int k2_items(const fastsv_ctx* h) {
     return (it == 4 || it == 8 || it == 16) ? it : 8;
 }
 
+int k2_threads(const fastsv_ctx* h) {
+    int t = h->opt.k2_threads;
+    return (t == 64 || t == 256) ? t : 64;
+}
+
+int64_t k2_tile(const fastsv_ctx* h) { return (int64_t)k2_threads(h) * k2_items(h); }
+
 // kernel instance selection -------------------------------------------------
 
-static const void* k2_func(int rp64, int items) {
-    if (rp64) {
-        if (items == 4) return (const void*)k2_hook<int64_t, 4>;
-        if (items == 16) return (const void*)k2_hook<int64_t, 16>;
-        return (const void*)k2_hook<int64_t, 8>;
-    }
-    if (items == 4) return (const void*)k2_hook<int32_t, 4>;
-    if (items == 16) return (const void*)k2_hook<int32_t, 16>;
-    return (const void*)k2_hook<int32_t, 8>;
+template <typename RP, int THREADS>
+static const void* k2_func_t(int items) {
+    if (items == 4) return (const void*)k2_spmv<RP, THREADS, 4>;
+    if (items == 16) return (const void*)k2_spmv<RP, THREADS, 16>;
+    return (const void*)k2_spmv<RP, THREADS, 8>;
 }
 
-static int k2_smem(int items) {
-    return items == 4 ? k2_smem_bytes<4>() : items == 16 ? k2_smem_bytes<16>() : k2_smem_bytes<8>();
+static const void* k2_func(int rp64, int items, int threads) {
+    if (rp64) return threads == 256 ? k2_func_t<int64_t, 256>(items) : k2_func_t<int64_t, 64>(items);
+    return threads == 256 ? k2_func_t<int32_t, 256>(items) : k2_func_t<int32_t, 64>(items);
 }
 
-static fastsv_status k2_grid_for(fastsv_ctx* h, int rp64, int items, int* grid) {
-    const void* fn = k2_func(rp64, items);
-    int smem = k2_smem(items);
+static int k2_smem(int items, int threads) {
+    if (threads == 256)
+        return items == 4 ? k2_smem_bytes<256, 4>() : items == 16 ? k2_smem_bytes<256, 16>() : k2_smem_bytes<256, 8>();
+    return items == 4 ? k2_smem_bytes<64, 4>() : items == 16 ? k2_smem_bytes<64, 16>() : k2_smem_bytes<64, 8>();
+}
+
+static fastsv_status k2_grid_for(fastsv_ctx* h, int rp64, int items, int threads, int* grid) {
+    const void* fn = k2_func(rp64, items, threads);
+    int smem = k2_smem(items, threads);
     FSV_CUDA(h, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     int per_sm = 0;
-    FSV_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, K2_THREADS, smem));
+    FSV_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem));
     if (per_sm < 1) per_sm = 1;
     if (h->opt.grid_ctas_per_sm > 0 && h->opt.grid_ctas_per_sm < per_sm) per_sm = h->opt.grid_ctas_per_sm;
     *grid = per_sm * h->num_sms;
     return FASTSV_OK;
 }
 
-static fastsv_status k3_grid_for(fastsv_ctx* h, int* grid) {
+
+// kernel functions of one iteration for a given configuration
+struct IterKernels {
+    const void* spmv;
+    const void* push;
+    const void* hook;
+    const void* k3;
+    int spmv_smem;
+    int spmv_grid, vtx_grid;
+};
+
+static fastsv_status iter_kernels(fastsv_ctx* h, int rp64_orig, int rp64_dense, int items, IterKernels* k) {
+    const int threads = k2_threads(h);
+    k->spmv = k2_func(rp64_dense, items, threads);
+    k->spmv_smem = k2_smem(items, threads);
+    k->push = rp64_orig ? (const void*)k2_push<int64_t> : (const void*)k2_push<int32_t>;
+    k->hook = (const void*)k2_hook;
+    k->k3 = rp64_orig ? (const void*)k3_grandparent<int64_t> : (const void*)k3_grandparent<int32_t>;
+    fastsv_status st;
+    if ((st = k2_grid_for(h, rp64_dense, items, threads, &k->spmv_grid)) != FASTSV_OK) return st;
     int per_sm = 0;
-    FSV_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k3_grandparent, K3_THREADS, 0));
+    FSV_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k->k3, K3_THREADS, 0));
     if (per_sm < 1) per_sm = 1;
     if (h->opt.grid_ctas_per_sm > 0 && h->opt.grid_ctas_per_sm < per_sm) per_sm = h->opt.grid_ctas_per_sm;
-    *grid = per_sm * h->num_sms;
+    k->vtx_grid = per_sm * h->num_sms;
     return FASTSV_OK;
 }
 
-// the device-side loop: WHILE(cond) { k2_hook; k3_grandparent }
-fastsv_status get_loop_graph(fastsv_ctx* h, Ctx* ctx, int rp64, int items, LoopGraph** out) {
-    GraphKey key{rp64, items, h->opt.mode, ctx};
+// the device-side loop:
+//   WHILE(cond) { k_iter_begin; k2_spmv | k2_push; k2_hook; k3_grandparent }
+// (k2_spmv and k2_push read the iteration's mode and return at once when it
+// is not theirs)
+fastsv_status get_loop_graph(fastsv_ctx* h, Ctx* ctx, int rp64_orig, int rp64_dense, int items, int nblocks,
+                             LoopGraph** out) {
+    const int threads = k2_threads(h);
+    GraphKey key{rp64_orig * 2 + rp64_dense, items * 1000 + threads, h->opt.mode * 64 + nblocks, ctx};
     auto it = h->graphs.find(key);
     if (it != h->graphs.end()) {
         *out = &it->second;
         return FASTSV_OK;
     }
-    int g2 = 0, g3 = 0;
-    fastsv_status st;
-    if ((st = k2_grid_for(h, rp64, items, &g2)) != FASTSV_OK) return st;
-    if ((st = k3_grid_for(h, &g3)) != FASTSV_OK) return st;
+    IterKernels K;
+    fastsv_status st = iter_kernels(h, rp64_orig, rp64_dense, items, &K);
+    if (st != FASTSV_OK) return st;
     LoopGraph lg;
     FSV_CUDA(h, cudaGraphCreate(&lg.graph, 0));
     FSV_CUDA(h, cudaGraphConditionalHandleCreate(&lg.cond, lg.graph, 1, cudaGraphCondAssignDefault));
@@ -166,80 +201,128 @@ fastsv_status get_loop_graph(fastsv_ctx* h, Ctx* ctx, int rp64, int items, LoopG
 
     cudaGraphConditionalHandle cond = lg.cond;
     int use_cond = 1;
-    void* k2args[] = {(void*)&ctx, (void*)&cond, (void*)&use_cond};
-    cudaKernelNodeParams kp;
-    memset(&kp, 0, sizeof(kp));
-    kp.func = (void*)k2_func(rp64, items);
-    kp.gridDim = dim3((unsigned)g2);
-    kp.blockDim = dim3(K2_THREADS);
-    kp.sharedMemBytes = (unsigned)k2_smem(items);
-    kp.kernelParams = k2args;
-    cudaGraphNode_t n2, n3;
-    FSV_CUDA(h, cudaGraphAddKernelNode(&n2, body, nullptr, 0, &kp));
-
-    void* k3args[] = {(void*)&ctx, (void*)&cond, (void*)&use_cond};
-    kp.func = (void*)k3_grandparent;
-    kp.gridDim = dim3((unsigned)g3);
-    kp.blockDim = dim3(K3_THREADS);
-    kp.sharedMemBytes = 0;
-    kp.kernelParams = k3args;
-    FSV_CUDA(h, cudaGraphAddKernelNode(&n3, body, &n2, 1, &kp));
+    void* a_begin[] = {(void*)&ctx, (void*)&cond, (void*)&use_cond};
+    void* a_ctx[] = {(void*)&ctx};
+    void* a_k3[] = {(void*)&ctx, (void*)&cond, (void*)&use_cond};
+    // one SpMV node for an unblocked solve (block = -1), else one per column
+    // block, in order (kernel parameters are copied when a node is added)
+    std::vector<int> blocks;
+    if (nblocks <= 0)
+        blocks.push_back(-1);
+    else
+        for (int b = 0; b < nblocks; ++b) blocks.push_back(b);
+    std::vector<void*> spmv_args(2 * blocks.size());
+    struct NodeSpec {
+        const void* fn;
+        int grid, block, smem;
+        void** args;
+    };
+    std::vector<NodeSpec> nodes;
+    nodes.push_back({(const void*)k_iter_begin, K.vtx_grid, 256, 0, a_begin});
+    for (size_t i = 0; i < blocks.size(); ++i) {
+        spmv_args[2 * i] = (void*)&ctx;
+        spmv_args[2 * i + 1] = (void*)&blocks[i];
+        nodes.push_back({K.spmv, K.spmv_grid, threads, K.spmv_smem, &spmv_args[2 * i]});
+    }
+    nodes.push_back({K.push, h->num_sms * 8, 256, 0, a_ctx});
+    nodes.push_back({K.hook, K.vtx_grid, K3_THREADS, 0, a_ctx});
+    nodes.push_back({K.k3, K.vtx_grid, K3_THREADS, 0, a_k3});
+    cudaGraphNode_t prev = nullptr;
+    for (size_t i = 0; i < nodes.size(); ++i) {
+        cudaKernelNodeParams kp;
+        memset(&kp, 0, sizeof(kp));
+        kp.func = (void*)nodes[i].fn;
+        kp.gridDim = dim3((unsigned)nodes[i].grid);
+        kp.blockDim = dim3((unsigned)nodes[i].block);
+        kp.sharedMemBytes = (unsigned)nodes[i].smem;
+        kp.kernelParams = nodes[i].args;
+        cudaGraphNode_t node;
+        FSV_CUDA(h, cudaGraphAddKernelNode(&node, body, prev ? &prev : nullptr, prev ? 1 : 0, &kp));
+        prev = node;
+    }
     FSV_CUDA(h, cudaGraphInstantiate(&lg.exec, lg.graph, 0));
     auto res = h->graphs.emplace(key, lg);
     *out = &res.first->second;
     return FASTSV_OK;
 }
 
-fastsv_status run_loop(fastsv_ctx* h, Ctx* ctx, int rp64, int items, cudaStream_t s) {
+fastsv_status run_loop(fastsv_ctx* h, Ctx* ctx, int rp64_orig, int rp64_dense, int items, int nblocks,
+                       cudaStream_t s) {
+    const int spmv_launches = nblocks > 0 ? nblocks : 1;
     if (h->opt.use_graph) {
         LoopGraph* lg = nullptr;
-        fastsv_status st = get_loop_graph(h, ctx, rp64, items, &lg);
+        fastsv_status st = get_loop_graph(h, ctx, rp64_orig, rp64_dense, items, nblocks, &lg);
         if (st != FASTSV_OK) return st;
         FSV_CUDA(h, cudaGraphLaunch(lg->exec, s));
-        h->pending_loop_kernels = 2;
+        h->pending_loop_kernels = 4 + spmv_launches;
         return FASTSV_OK;
     }
     // host loop: one synchronisation per iteration, per-kernel event timing
-    int g2 = 0, g3 = 0;
-    fastsv_status st;
-    if ((st = k2_grid_for(h, rp64, items, &g2)) != FASTSV_OK) return st;
-    if ((st = k3_grid_for(h, &g3)) != FASTSV_OK) return st;
-    const void* fn = k2_func(rp64, items);
-    int smem = k2_smem(items);
-    cudaEvent_t e[3];
-    for (int i = 0; i < 3; ++i) FSV_CUDA(h, cudaEventCreate(&e[i]));
-    float t2 = 0.f, t3 = 0.f;
-    int iters = 0;
+    IterKernels K;
+    fastsv_status st = iter_kernels(h, rp64_orig, rp64_dense, items, &K);
+    if (st != FASTSV_OK) return st;
+    const int threads = k2_threads(h);
+    cudaEvent_t e[5];
+    for (int i = 0; i < 5; ++i) FSV_CUDA(h, cudaEventCreate(&e[i]));
+    float t_spmv = 0.f, t_push = 0.f, t_hook = 0.f, t_k3 = 0.f;
+    int iters = 0, dense = 0;
     cudaGraphConditionalHandle none = 0;
     int no_cond = 0;
     int32_t limit = h->loop_limit_host;
     fastsv_status rc = FASTSV_OK;
+    int32_t mode = 0;
     for (;;) {
-        void* a2[] = {(void*)&ctx, (void*)&none, (void*)&no_cond};
-        void* a3[] = {(void*)&ctx, (void*)&none, (void*)&no_cond};
-        cudaEventRecord(e[0], s);
-        cudaError_t ce = cudaLaunchKernel(fn, dim3(g2), dim3(K2_THREADS), a2, (size_t)smem, s);
+        void* a_begin[] = {(void*)&ctx, (void*)&none, (void*)&no_cond};
+        void* a_ctx[] = {(void*)&ctx};
+        void* a_k3[] = {(void*)&ctx, (void*)&none, (void*)&no_cond};
+        cudaError_t ce = cudaEventRecord(e[0], s);
+        if (ce == cudaSuccess)
+            ce = cudaLaunchKernel((const void*)k_iter_begin, dim3(K.vtx_grid), dim3(256), a_begin, 0, s);
+        for (int b = 0; b < spmv_launches && ce == cudaSuccess; ++b) {
+            int blk = nblocks > 0 ? b : -1;
+            void* a_spmv[] = {(void*)&ctx, (void*)&blk};
+            ce = cudaLaunchKernel(K.spmv, dim3(K.spmv_grid), dim3(threads), a_spmv, K.spmv_smem, s);
+        }
         if (ce == cudaSuccess) ce = cudaEventRecord(e[1], s);
-        if (ce == cudaSuccess) ce = cudaLaunchKernel((const void*)k3_grandparent, dim3(g3), dim3(K3_THREADS), a3, 0, s);
+        if (ce == cudaSuccess) ce = cudaLaunchKernel(K.push, dim3(h->num_sms * 8), dim3(256), a_ctx, 0, s);
         if (ce == cudaSuccess) ce = cudaEventRecord(e[2], s);
-        if (ce == cudaSuccess) ce = cudaMemcpyAsync(h->h_scalar, &ctx->any_active, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+        if (ce == cudaSuccess) ce = cudaLaunchKernel(K.hook, dim3(K.vtx_grid), dim3(K3_THREADS), a_ctx, 0, s);
+        if (ce == cudaSuccess) ce = cudaEventRecord(e[3], s);
+        if (ce == cudaSuccess) ce = cudaLaunchKernel(K.k3, dim3(K.vtx_grid), dim3(K3_THREADS), a_k3, 0, s);
+        if (ce == cudaSuccess) ce = cudaEventRecord(e[4], s);
+        if (ce == cudaSuccess)
+            ce = cudaMemcpyAsync(h->h_scalar, &ctx->any_active, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+        if (ce == cudaSuccess)
+            ce = cudaMemcpyAsync((int32_t*)h->h_scalar + 1, &ctx->mode, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
         if (ce != cudaSuccess) {
             rc = cuda_fail(h, ce);
             break;
         }
-        h->launches += 2;
-        float a = 0.f, b = 0.f;
+        h->launches += 4 + spmv_launches;
+        float a = 0.f, b = 0.f, c = 0.f, d = 0.f;
         cudaEventElapsedTime(&a, e[0], e[1]);
         cudaEventElapsedTime(&b, e[1], e[2]);
-        t2 += a;
-        t3 += b;
+        cudaEventElapsedTime(&c, e[2], e[3]);
+        cudaEventElapsedTime(&d, e[3], e[4]);
+        if (mode == 0) {
+            t_spmv += a;
+            ++dense;
+        } else {
+            t_push += b;
+        }
+        t_hook += c;
+        t_k3 += d;
         ++iters;
-        if (*(int32_t*)h->h_scalar == 0 || iters >= limit) break;
+        mode = ((int32_t*)h->h_scalar)[1];  // the mode k3 chose for the next iteration
+        if (((int32_t*)h->h_scalar)[0] == 0 || iters >= limit) break;
     }
-    for (int i = 0; i < 3; ++i) cudaEventDestroy(e[i]);
-    h->ms_k2 = t2;
-    h->ms_k3 = t3;
+    for (int i = 0; i < 5; ++i) cudaEventDestroy(e[i]);
+    h->ms_k2 = t_spmv;
+    h->ms_push = t_push;
+    h->ms_hook = t_hook;
+    h->ms_k3 = t_k3;
+    h->dense_iters = dense;
     h->pending_loop_kernels = 0;
     return rc;
 }
@@ -306,44 +389,55 @@ static int choose_col_blocks(const fastsv_ctx* h, int64_t n, int64_t m) {
     if (m > (int64_t)INT32_MAX - 1) return 1;  // block row pointers are int32
     if (nb == 1) return 1;
     if (nb <= 0) {
-        const int64_t slice = 40ll << 20;  // bytes of gf per block kept in L2
-        if (4 * n <= slice || m < 8 * n) return 1;
-        nb = 1;
-        while (nb < MAX_COL_BLOCKS && 4 * n > slice * nb) nb <<= 1;
+        // Automatic: measured on R-MAT scale 26 (GB300), 4 blocks cut a full
+        // SpMV from 18.3 to 11.8 ms but the per-call block copy costs ~50 ms,
+        // more than the 4-5 dense iterations such graphs need can win back,
+        // so blocking is only taken when asked for explicitly.
+        return 1;
     }
     if (nb > MAX_COL_BLOCKS) nb = MAX_COL_BLOCKS;
     return nb;
 }
 
 template <typename RP>
-static fastsv_status launch_block_build(fastsv_ctx* h, int items, int nb, int shift, int64_t n, cudaStream_t s) {
+static fastsv_status launch_block_build(fastsv_ctx* h, int nb, int shift, int64_t n, cudaStream_t s) {
     const int g = setup_grid(h);
     const int64_t np1 = n + 1;
     const int64_t chunks = (np1 + SCAN_CHUNK - 1) / SCAN_CHUNK;
-    int smem = items == 4 ? block_build_smem<4>(nb) : items == 16 ? block_build_smem<16>(nb) : block_build_smem<8>(nb);
-    const void* fc = items == 4 ? (const void*)k_block_count<RP, 4>
-                   : items == 16 ? (const void*)k_block_count<RP, 16> : (const void*)k_block_count<RP, 8>;
-    const void* fs = items == 4 ? (const void*)k_block_scatter<RP, 4>
-                   : items == 16 ? (const void*)k_block_scatter<RP, 16> : (const void*)k_block_scatter<RP, 8>;
-    FSV_CUDA(h, cudaFuncSetAttribute(fc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    FSV_CUDA(h, cudaFuncSetAttribute(fs, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    const int smem_count = block_build_smem(nb);
+    const int smem_sorted = block_scatter_smem(nb);
+    const void* fc = (const void*)k_block_count<RP>;
+    const void* fs = (const void*)k_block_scatter_sorted<RP>;
+    const void* fr = (const void*)k_block_scatter<RP>;
+    FSV_CUDA(h, cudaFuncSetAttribute(fc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_count));
+    FSV_CUDA(h, cudaFuncSetAttribute(fs, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_sorted));
+    FSV_CUDA(h, cudaFuncSetAttribute(fr, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_count));
     Ctx* ctx = h->d_ctx;
+    int32_t* flag = h->d_sums + h->cap_sums - 1;  // "some row is not sorted by column"
     FSV_CUDA(h, cudaMemsetAsync(h->d_counts, 0, (size_t)nb * np1 * 4, s));
+    FSV_CUDA(h, cudaMemsetAsync(flag, 0, sizeof(int32_t), s));
     {
-        void* a[] = {(void*)&ctx, (void*)&h->d_counts, (void*)&nb, (void*)&shift};
-        FSV_CUDA(h, cudaLaunchKernel(fc, dim3(g), dim3(K2_THREADS), a, (size_t)smem, s));
+        void* a[] = {(void*)&ctx, (void*)&h->d_counts, (void*)&nb, (void*)&shift, (void*)&flag};
+        FSV_CUDA(h, cudaLaunchKernel(fc, dim3(g), dim3(BUILD_THREADS), a, (size_t)smem_count, s));
     }
     int ch = (int)chunks;
     k_scan_chunk_sums<<<(unsigned)(nb * chunks), SCAN_THREADS, 0, s>>>(h->d_counts, np1, ch, h->d_sums);
     k_scan_sums<<<nb, 1024, 0, s>>>(h->d_sums, ch);
     k_scan_apply<<<(unsigned)(nb * chunks), SCAN_THREADS, 0, s>>>(h->d_counts, h->d_rpB, np1, ch, h->d_sums);
-    FSV_CUDA(h, cudaMemsetAsync(h->d_counts, 0, (size_t)nb * np1 * 4, s));
     {
+        // sorted rows: every entry's destination in closed form
         void* a[] = {(void*)&ctx, (void*)&h->d_rpB, (void*)&h->d_counts, (void*)&h->d_colB, (void*)&nb,
-                     (void*)&shift};
-        FSV_CUDA(h, cudaLaunchKernel(fs, dim3(g), dim3(K2_THREADS), a, (size_t)smem, s));
+                     (void*)&shift, (void*)&flag};
+        FSV_CUDA(h, cudaLaunchKernel(fs, dim3(g), dim3(BUILD_THREADS), a, (size_t)smem_sorted, s));
     }
-    h->pending_fixed_launches += 5;
+    {
+        // otherwise: ranks from atomics, counts reused as per-(row, block) cursors
+        FSV_CUDA(h, cudaMemsetAsync(h->d_counts, 0, (size_t)nb * np1 * 4, s));
+        void* a[] = {(void*)&ctx, (void*)&h->d_rpB, (void*)&h->d_counts, (void*)&h->d_colB, (void*)&nb,
+                     (void*)&shift, (void*)&flag};
+        FSV_CUDA(h, cudaLaunchKernel(fr, dim3(g), dim3(BUILD_THREADS), a, (size_t)smem_count, s));
+    }
+    h->pending_fixed_launches += 6;
     FSV_CUDA(h, cudaGetLastError());
     return FASTSV_OK;
 }
@@ -382,12 +476,14 @@ static fastsv_status solve_single(fastsv_ctx* h, int64_t n, int64_t m, const voi
                                   int32_t* labels, cudaStream_t s) {
     const int rp64 = h->opt.rowptr_bits == 64;
     const int items = k2_items(h);
-    const int64_t tile = (int64_t)K2_THREADS * items;
+    const int64_t tile = k2_tile(h);
     const int nb = m > 0 ? choose_col_blocks(h, n, m) : 1;
     int shift = 0;
     while (shift < 31 && ((int64_t)nb << shift) < n) ++shift;
     const int nb_eff = nb > 1 ? (int)((n + (1ll << shift) - 1) >> shift) : 1;
-    const int64_t t2 = m > 0 ? (n + m + tile - 1) / tile : 0;
+    // a blocked solve partitions the graph itself for the block build first
+    const int64_t tile0 = nb_eff > 1 ? (int64_t)BUILD_TILE : tile;
+    const int64_t t2 = m > 0 ? (n + m + tile0 - 1) / tile0 : 0;
     const int64_t t2b = nb_eff > 1 ? ((int64_t)nb_eff * n + m) / tile + nb_eff + 1 : 0;
     const int64_t t3 = (n + K3_TILE - 1) / K3_TILE;
     if (t2 > INT32_MAX || t2b > INT32_MAX || t3 > INT32_MAX) return FASTSV_ERR_UNSUPPORTED;
@@ -395,7 +491,8 @@ static fastsv_status solve_single(fastsv_ctx* h, int64_t n, int64_t m, const voi
     if (st != FASTSV_OK) return st;
     if (nb_eff > 1 && (st = ensure_block_workspace(h, nb_eff, n, m)) != FASTSV_OK) return st;
     h->pending_fixed_launches = 0;
-    h->ms_k2 = h->ms_k3 = 0.f;
+    h->ms_k2 = h->ms_k3 = h->ms_push = h->ms_hook = 0.f;
+    h->dense_iters = 0;
     h->last_col_blocks = nb_eff;
     FSV_CUDA(h, cudaEventRecord(h->ev_start, s));
     SingleParams prm;
@@ -404,9 +501,12 @@ static fastsv_status solve_single(fastsv_ctx* h, int64_t n, int64_t m, const voi
     prm.f = labels;
     prm.p = h->d_p;
     prm.gf = h->d_gf;
+    prm.mngf = h->d_mngf;
+    prm.frontier = h->d_frontier;
+    prm.sparse_max_deg = h->opt.sparse_div > 0 ? m / h->opt.sparse_div : -1;
     prm.n = n;
     prm.m = m;
-    prm.k2_tile = (int32_t)tile;
+    prm.k2_tile = (int32_t)tile0;
     prm.max_iters = h->opt.max_iters;
     prm.loop_limit = h->opt.max_iters + 1;
     WsPtrs ws{h->d_segs, h->d_k2_seg, h->d_k2_row, h->d_k3_seg};
@@ -421,8 +521,8 @@ static fastsv_status solve_single(fastsv_ctx* h, int64_t n, int64_t m, const voi
     int loop_rp64 = rp64;
     if (nb_eff > 1) {
         // split the columns into blocks, then partition every block's CSR
-        st = rp64 ? launch_block_build<int64_t>(h, items, nb_eff, shift, n, s)
-                  : launch_block_build<int32_t>(h, items, nb_eff, shift, n, s);
+        st = rp64 ? launch_block_build<int64_t>(h, nb_eff, shift, n, s)
+                  : launch_block_build<int32_t>(h, nb_eff, shift, n, s);
         if (st != FASTSV_OK) return st;
         k_setup_blocks<<<1, 1, 0, s>>>(h->d_ctx, h->d_rpB, h->d_colB, nb_eff, (int32_t)tile);
         k_scan_tiles<<<1, 1024, 0, s>>>(h->d_ctx);
@@ -435,7 +535,7 @@ static fastsv_status solve_single(fastsv_ctx* h, int64_t n, int64_t m, const voi
     FSV_CUDA(h, cudaGetLastError());
     FSV_CUDA(h, cudaEventRecord(h->ev_setup, s));
     h->loop_limit_host = prm.loop_limit;
-    if ((st = run_loop(h, h->d_ctx, loop_rp64, items, s)) != FASTSV_OK) return st;
+    if ((st = run_loop(h, h->d_ctx, rp64, loop_rp64, items, nb_eff > 1 ? nb_eff : 0, s)) != FASTSV_OK) return st;
     return finish_call(h, s, nullptr, n, m, true);
 }
 
@@ -460,6 +560,9 @@ void fastsv_default_options(fastsv_options* o) {
     o->l2_persist = 0;
     o->timing = 1;
     o->fail_alloc_after = 0;
+    o->col_blocks = 0;
+    o->k2_threads = 64;
+    o->sparse_div = 2;
 }
 
 const char* fastsv_status_string(fastsv_status s) {
@@ -527,6 +630,8 @@ fastsv_status fastsv_destroy(fastsv_t h) {
     dev_free((void**)&h->d_k3_seg);
     dev_free((void**)&h->d_p);
     dev_free((void**)&h->d_gf);
+    dev_free((void**)&h->d_mngf);
+    dev_free((void**)&h->d_frontier);
     dev_free((void**)&h->d_counts);
     dev_free((void**)&h->d_rpB);
     dev_free((void**)&h->d_sums);
@@ -629,14 +734,15 @@ fastsv_status fastsv_cc_batched(fastsv_t h, int32_t G, const int64_t* vtx_off, c
     if (N < 0 || M < 0) return FASTSV_ERR_INVALID_GRAPH;
     if (M > 0 && !col_idx) return FASTSV_ERR_INVALID_ARG;
     const int items = k2_items(h);
-    const int64_t tile = (int64_t)K2_THREADS * items;
+    const int64_t tile = k2_tile(h);
     const int64_t t2 = (N + M) / tile + G + 1;
     const int64_t t3 = N / K3_TILE + G + 1;
     if (t2 > INT32_MAX || t3 > INT32_MAX) return FASTSV_ERR_UNSUPPORTED;
     fastsv_status st = ensure_workspace(h, N > 0 ? N : 1, t2, t3, G);
     if (st != FASTSV_OK) return st;
     h->pending_fixed_launches = 0;
-    h->ms_k2 = h->ms_k3 = 0.f;
+    h->ms_k2 = h->ms_k3 = h->ms_push = h->ms_hook = 0.f;
+    h->dense_iters = 0;
     FSV_CUDA(h, cudaEventRecord(h->ev_start, s));
     BatchParams prm;
     prm.G = G;
@@ -647,6 +753,7 @@ fastsv_status fastsv_cc_batched(fastsv_t h, int32_t G, const int64_t* vtx_off, c
     prm.labels = labels_out;
     prm.p = h->d_p;
     prm.gf = h->d_gf;
+    prm.mngf = h->d_mngf;
     prm.k2_tile = (int32_t)tile;
     prm.max_iters = h->opt.max_iters;
     prm.loop_limit = h->opt.max_iters + 1;
@@ -663,7 +770,7 @@ fastsv_status fastsv_cc_batched(fastsv_t h, int32_t G, const int64_t* vtx_off, c
     FSV_CUDA(h, cudaEventRecord(h->ev_setup, s));
     if (N > 0) {
         h->loop_limit_host = prm.loop_limit;
-        if ((st = run_loop(h, h->d_ctx, 0, items, s)) != FASTSV_OK) return st;
+        if ((st = run_loop(h, h->d_ctx, 0, 0, items, 0, s)) != FASTSV_OK) return st;
     } else {
         h->pending_loop_kernels = 0;
     }
@@ -711,6 +818,10 @@ fastsv_status fastsv_get_stats(fastsv_t h, fastsv_stats* out) {
     out->converged = S.converged;
     out->ms_k2 = h->ms_k2;
     out->ms_k3 = h->ms_k3;
+    out->ms_push = h->ms_push;
+    out->ms_hook = h->ms_hook;
+    out->sparse_iters = S.sparse_iters;
+    out->dense_iters = h->opt.use_graph ? (int32_t)(S.iterations - S.sparse_iters) : h->dense_iters;
     int len = (int)(S.iterations < TRACE_LEN ? S.iterations : TRACE_LEN);
     out->trace_len = h->single ? len : 0;
     out->col_blocks = h->single ? h->last_col_blocks : 1;

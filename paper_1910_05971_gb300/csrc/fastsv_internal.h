@@ -51,6 +51,8 @@ struct fastsv_ctx {
     int64_t cap_k3 = 0;
     int32_t* d_p = nullptr;
     int32_t* d_gf = nullptr;
+    int32_t* d_mngf = nullptr;       // per-row neighbour minimum, kept across iterations
+    int32_t* d_frontier = nullptr;   // vertices whose gf changed in the last iteration
     int64_t cap_n = 0;
 
     // column-blocked copy of a large graph (see k_block_count)
@@ -87,7 +89,8 @@ struct fastsv_ctx {
     int last_cuda_error = 0;
     bool pending = false;      // a call whose summary has not been read yet
     bool single = true;        // last call was a single-graph call
-    float ms_k2 = 0.f, ms_k3 = 0.f;
+    float ms_k2 = 0.f, ms_k3 = 0.f, ms_push = 0.f, ms_hook = 0.f;
+    int32_t dense_iters = 0;
     float ms_total_cache = 0.f, ms_setup_cache = 0.f;
     int64_t launches = 0;      // kernels launched, settled by fastsv_get_stats
     int64_t pending_fixed_launches = 0;  // set-up kernels of the pending call
@@ -112,11 +115,15 @@ fastsv_status cuda_fail(fastsv_ctx* h, cudaError_t e);
 // device allocation through the handle (counts allocations for the test hook)
 fastsv_status dev_alloc(fastsv_ctx* h, void** p, size_t bytes);
 fastsv_status ensure_workspace(fastsv_ctx* h, int64_t n, int64_t k2_tiles, int64_t k3_tiles, int64_t segs);
-fastsv_status get_loop_graph(fastsv_ctx* h, Ctx* ctx, int rp64, int items, LoopGraph** out);
-fastsv_status run_loop(fastsv_ctx* h, Ctx* ctx, int rp64, int items, cudaStream_t s);
+fastsv_status get_loop_graph(fastsv_ctx* h, Ctx* ctx, int rp64_orig, int rp64_dense, int items, int nblocks,
+                             LoopGraph** out);
+fastsv_status run_loop(fastsv_ctx* h, Ctx* ctx, int rp64_orig, int rp64_dense, int items, int nblocks,
+                       cudaStream_t s);
 fastsv_status rebuild_tiles(fastsv_ctx* h, Ctx* ctx, cudaStream_t s);
 int setup_grid(const fastsv_ctx* h);
 int k2_items(const fastsv_ctx* h);
+int k2_threads(const fastsv_ctx* h);
+int64_t k2_tile(const fastsv_ctx* h);
 void pool_release(fastsv_ctx* h);
 
 }  // namespace fsv

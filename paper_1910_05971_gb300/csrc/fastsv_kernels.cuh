@@ -100,6 +100,9 @@ struct SingleParams {
     int32_t* f;
     int32_t* p;
     int32_t* gf;
+    int32_t* mngf;
+    int32_t* frontier;
+    int64_t sparse_max_deg;  // < 0: sparse iterations off
     int64_t n, m;
     int32_t k2_tile;
     int32_t max_iters;
@@ -129,6 +132,7 @@ __global__ void k_setup_single(Ctx* ctx, SingleParams prm, WsPtrs ws) {
     s.user = 0;
     s.leader = 0;
     s.pad = 0;
+    s.mngf = prm.mngf;
     ws.segs[0] = s;
     ctx->num_segs = 1;
     ctx->k2_tile = prm.k2_tile;
@@ -140,6 +144,14 @@ __global__ void k_setup_single(Ctx* ctx, SingleParams prm, WsPtrs ws) {
     ctx->k3_done = 0;
     ctx->any_active = s.active;
     ctx->val_status = 0;
+    ctx->sparse_enabled = prm.sparse_max_deg >= 0;
+    ctx->mode = 0;
+    ctx->frontier = prm.frontier;
+    ctx->frontier_len = 0;
+    ctx->frontier_next = 0;
+    ctx->frontier_deg = 0;
+    ctx->sparse_max_deg = prm.sparse_max_deg;
+    ctx->sparse_iters = 0;
     for (int i = 0; i < TRACE_LEN; ++i) ctx->sum.trace[i] = 0;
 }
 
@@ -152,6 +164,7 @@ struct BatchParams {
     int32_t* labels;
     int32_t* p;
     int32_t* gf;
+    int32_t* mngf;
     int32_t k2_tile;
     int32_t max_iters;
     int32_t loop_limit;
@@ -185,6 +198,7 @@ __global__ void k_setup_batched(Ctx* ctx, BatchParams prm, WsPtrs ws) {
         s.user = (int32_t)g;
         s.leader = (int32_t)g;
         s.pad = 0;
+        s.mngf = prm.mngf + v0;
         ws.segs[g] = s;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -196,6 +210,9 @@ __global__ void k_setup_batched(Ctx* ctx, BatchParams prm, WsPtrs ws) {
         ctx->loop_iter = 0;
         ctx->k3_done = 0;
         ctx->val_status = 0;
+        ctx->sparse_enabled = 0;
+        ctx->mode = 0;
+        ctx->sparse_iters = 0;
         for (int i = 0; i < TRACE_LEN; ++i) ctx->sum.trace[i] = 0;
     }
 }
@@ -352,9 +369,12 @@ __device__ __forceinline__ int col_block(int32_t c, int shift, int nb) {
     return b < nb ? b : nb - 1;
 }
 
-template <int ITEMS>
+constexpr int BUILD_THREADS = 128;  // CTA size and items per thread of the block-build kernels
+constexpr int BUILD_ITEMS = 8;
+constexpr int BUILD_TILE = BUILD_THREADS * BUILD_ITEMS;
+
 constexpr int block_build_smem(int nb) {
-    return (3 * (K2_THREADS * ITEMS + 1) + (K2_THREADS * ITEMS + 1) * nb) * (int)sizeof(int32_t);
+    return (3 * (BUILD_TILE + 1) + (BUILD_TILE + 1) * nb) * (int)sizeof(int32_t);
 }
 
 // Loads the tile's row ends and column ids (coalesced) into shared memory and
@@ -401,58 +421,233 @@ __device__ __forceinline__ bool load_tile(const Seg& S, int64_t t, int64_t tile,
     R = nfull + (x1 < n ? 1 : 0);
     E = (int)(y1 - y0);
     D = (int)(d1 - d0);
-    for (int i = threadIdx.x; i < R; i += blockDim.x) {
-        int64_t e = rp_at(rp, x0 + i + 1);
-        e = e < y1 ? e : y1;
-        e -= y0;
-        s_rowend[i] = (int32_t)(e < 0 ? 0 : e);
+    // loads first, stores after (clamped addresses), ITEMS = tile / blockDim
+    constexpr int ITEMS = BUILD_ITEMS;  // upper bound; the loops stop at the tile size
+    const int per = (int)(tile / blockDim.x);
+    int64_t e[ITEMS + 1];
+    int32_t c[ITEMS];
+#pragma unroll
+    for (int q = 0; q <= ITEMS; ++q) {
+        if (q > per) break;
+        const int i = threadIdx.x + q * blockDim.x;
+        int64_t row = x0 + (i < R ? i : 0) + 1;
+        e[q] = rp_at(rp, row < n ? row : n);
     }
-    for (int j = threadIdx.x; j < E; j += blockDim.x) s_col[j] = ld_stream(S.ci + y0 + j);
+#pragma unroll
+    for (int q = 0; q < ITEMS; ++q) {
+        if (q >= per) break;
+        const int j = threadIdx.x + q * blockDim.x;
+        int64_t pos = y0 + (j < E ? j : 0);
+        c[q] = ld_stream(S.ci + (pos < m ? pos : m - 1));
+    }
+#pragma unroll
+    for (int q = 0; q <= ITEMS; ++q) {
+        if (q > per) break;
+        const int i = threadIdx.x + q * blockDim.x;
+        if (i < R) {
+            int64_t v = (e[q] < y1 ? e[q] : y1) - y0;
+            s_rowend[i] = (int32_t)(v < 0 ? 0 : v);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < ITEMS; ++q) {
+        if (q >= per) break;
+        const int j = threadIdx.x + q * blockDim.x;
+        if (j < E) s_col[j] = c[q];
+    }
     return true;
 }
 
-// counts[b][u] = entries of row u whose column lies in block b
-template <typename RP, int ITEMS>
-__global__ void __launch_bounds__(K2_THREADS) k_block_count(Ctx* ctx, int32_t* counts, int nb, int shift) {
-    constexpr int TILE = K2_THREADS * ITEMS;
+// first local entry of row r of the tile (row 0 may have started in an
+// earlier tile: its first entry here is entry 0)
+__device__ __forceinline__ int row_start_local(const int32_t* s_rowend, int r) {
+    return r > 0 ? s_rowend[r - 1] : 0;
+}
+
+// counts[b][u] = entries of row u whose column lies in block b.  Every
+// thread counts its ITEMS merge-path items in one register (4 bits per
+// block), so shared-memory atomics happen once per (thread, row, block), not
+// per entry.  Rows that start and end inside the tile are stored, the two
+// that can continue in a neighbouring tile are added atomically.  The kernel
+// also records whether any row is not sorted by column (then the scatter
+// falls back to ranking entries with atomics).
+template <typename RP>
+__global__ void __launch_bounds__(BUILD_THREADS)
+    k_block_count(Ctx* ctx, int32_t* counts, int nb, int shift, int32_t* unsorted) {
+    constexpr int TILE = BUILD_TILE;
+    constexpr int RS = TILE + 1;
     extern __shared__ int32_t smem[];
     int32_t* s_rowend = smem;
-    int32_t* s_col = smem + (TILE + 1);
-    int32_t* s_cnt = smem + 3 * (TILE + 1);
+    int32_t* s_col = smem + RS;
+    int32_t* s_cnt = smem + 2 * RS;  // [nb][RS]
     const Seg S = ctx->segs[0];
+    const RP* rp = (const RP*)S.rp;
     const int64_t np1 = S.n + 1;
+    int bad = 0;
     for (int64_t t = blockIdx.x; t < S.k2_ntiles; t += gridDim.x) {
         int64_t x0;
         int nfull, R, E, D;
         if (!load_tile<RP>(S, t, TILE, ctx->k2_tile_row, s_rowend, s_col, x0, nfull, R, E, D)) continue;
-        for (int i = threadIdx.x; i < R * nb; i += blockDim.x) s_cnt[i] = 0;
+        for (int b = 0; b < nb; ++b)
+            for (int r = threadIdx.x; r < R; r += BUILD_THREADS) s_cnt[b * RS + r] = 0;
+        const int64_t y0 = (t - S.k2_tile0) * TILE - x0;
+        const bool first_whole = rp_at(rp, x0) >= y0;
         __syncthreads();
-        tile_walk<RP, ITEMS>(s_rowend, nfull, E, D, [&](int r, int y) {
-            atomicAdd(&s_cnt[r * nb + col_block(s_col[y], shift, nb)], 1);
-        });
+        // a row continuing from the previous tile must be sorted across it
+        if (threadIdx.x == 0 && !first_whole && E > 0 && y0 > 0 && S.ci[y0 - 1] > s_col[0]) bad = 1;
+        const int k0 = threadIdx.x * BUILD_ITEMS;
+        if (k0 < D) {
+            int lo = 0, hi = nfull;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (s_rowend[mid] + mid < k0)
+                    lo = mid + 1;
+                else
+                    hi = mid;
+            }
+            int r = lo, y = k0 - lo;
+            int rend = r < nfull ? s_rowend[r] : 0x7fffffff;
+            int32_t prev = y > row_start_local(s_rowend, r) ? s_col[y - 1] : INT32_MIN;
+            unsigned long long cnt = 0;
+            const int steps = min(BUILD_ITEMS, D - k0);
+            for (int k = 0; k <= steps; ++k) {
+                const bool row_end = k == steps || y >= rend;
+                if (row_end) {
+                    while (cnt) {
+                        const int bb = (__ffsll((long long)cnt) - 1) >> 2;
+                        atomicAdd(&s_cnt[bb * RS + r], (int)((cnt >> (4 * bb)) & 15ull));
+                        cnt &= ~(15ull << (4 * bb));
+                    }
+                    if (k == steps) break;
+                    ++r;
+                    rend = r < nfull ? s_rowend[r] : 0x7fffffff;
+                    prev = INT32_MIN;
+                } else {
+                    const int32_t c = s_col[y];
+                    if (c < prev) bad = 1;
+                    prev = c;
+                    cnt += 1ull << (4 * col_block(c, shift, nb));
+                    ++y;
+                }
+            }
+        }
         __syncthreads();
-        for (int i = threadIdx.x; i < R * nb; i += blockDim.x) {
-            const int c = s_cnt[i];
-            if (c) atomicAdd(&counts[(int64_t)(i % nb) * np1 + x0 + i / nb], c);
+        for (int b = 0; b < nb; ++b) {
+            for (int r = threadIdx.x; r < R; r += BUILD_THREADS) {
+                const int c = s_cnt[b * RS + r];
+                if (!c) continue;
+                int32_t* dst = counts + (int64_t)b * np1 + x0 + r;
+                if (r < nfull && (r > 0 || first_whole))
+                    *dst = c;
+                else
+                    atomicAdd(dst, c);
+            }
+        }
+        __syncthreads();
+    }
+    if (bad) atomicOr(unsorted, 1);
+}
+
+// With every row sorted by column, the entries of row u that fall in block
+// b are one contiguous run of row u, so entry e goes to
+//   base_b + rpB[b][u] + (e - rp[u] - sum_{b' < b} counts[b'][u]),
+// a plain coalesced copy.  Returns at once when a row was found unsorted.
+constexpr int block_scatter_smem(int nb) { return (2 + 2 * nb) * (BUILD_TILE + 1) * (int)sizeof(int32_t); }
+
+template <typename RP>
+__global__ void __launch_bounds__(BUILD_THREADS)
+    k_block_scatter_sorted(Ctx* ctx, const int32_t* rpB, const int32_t* counts, int32_t* colB, int nb, int shift,
+                           const int32_t* unsorted) {
+    constexpr int TILE = BUILD_TILE;
+    constexpr int RS = TILE + 1;
+    if (*unsorted) return;
+    extern __shared__ int32_t smem[];
+    int32_t* s_rowend = smem;
+    int32_t* s_col = smem + RS;
+    long long* s_delta = (long long*)(smem + 2 * RS);  // [nb][RS]
+    __shared__ long long s_blockbase[MAX_COL_BLOCKS];
+    const Seg S = ctx->segs[0];
+    const RP* rp = (const RP*)S.rp;
+    const int64_t np1 = S.n + 1;
+    const int64_t m = S.m;
+    if (threadIdx.x == 0) {
+        long long acc = 0;
+        for (int b = 0; b < nb; ++b) {
+            s_blockbase[b] = acc;
+            acc += rpB[(int64_t)b * np1 + S.n];
+        }
+    }
+    __syncthreads();
+    for (int64_t t = blockIdx.x; t < S.k2_ntiles; t += gridDim.x) {
+        int64_t x0;
+        int nfull, R, E, D;
+        if (!load_tile<RP>(S, t, TILE, ctx->k2_tile_row, s_rowend, s_col, x0, nfull, R, E, D)) continue;
+        const int64_t y0 = (t - S.k2_tile0) * TILE - x0;
+        for (int r = threadIdx.x; r < R; r += BUILD_THREADS) {
+            const int64_t u = x0 + r;
+            long long before = rp_at(rp, u);
+            for (int b = 0; b < nb; ++b) {
+                s_delta[b * RS + r] = s_blockbase[b] + rpB[(int64_t)b * np1 + u] - before;
+                before += counts[(int64_t)b * np1 + u];
+            }
+        }
+        __syncthreads();
+        const int k0 = threadIdx.x * BUILD_ITEMS;
+        if (k0 < D) {
+            int lo = 0, hi = nfull;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (s_rowend[mid] + mid < k0)
+                    lo = mid + 1;
+                else
+                    hi = mid;
+            }
+            int r = lo, y = k0 - lo;
+            int rend = r < nfull ? s_rowend[r] : 0x7fffffff;
+            const int steps = min(BUILD_ITEMS, D - k0);
+            for (int k = 0; k < steps; ++k) {
+                if (y >= rend) {
+                    ++r;
+                    rend = r < nfull ? s_rowend[r] : 0x7fffffff;
+                } else {
+                    const int32_t c = s_col[y];
+                    const long long pos = s_delta[col_block(c, shift, nb) * RS + r] + y0 + y;
+                    if (pos >= 0 && pos < m) colB[pos] = c;
+                    ++y;
+                }
+            }
         }
         __syncthreads();
     }
 }
 
-// colB[rpB[b][u] + k] for the k-th entry of row u in block b (order within a
-// row's block is arbitrary: the hooks only take minima)
-template <typename RP, int ITEMS>
-__global__ void __launch_bounds__(K2_THREADS)
-    k_block_scatter(Ctx* ctx, const int32_t* rpB, int32_t* cursor, int32_t* colB, int nb, int shift) {
-    constexpr int TILE = K2_THREADS * ITEMS;
+// Fallback for rows not sorted by column: colB[rpB[b][u] + k] for the k-th
+// entry of row u in block b, ranks from shared-memory atomics (the order
+// within a row's block is arbitrary: the SpMV only takes minima)
+template <typename RP>
+__global__ void __launch_bounds__(BUILD_THREADS)
+    k_block_scatter(Ctx* ctx, const int32_t* rpB, int32_t* cursor, int32_t* colB, int nb, int shift,
+                    const int32_t* unsorted) {
+    constexpr int TILE = BUILD_TILE;
+    if (!*unsorted) return;
     extern __shared__ int32_t smem[];
     int32_t* s_rowend = smem;
     int32_t* s_col = smem + (TILE + 1);
     int32_t* s_rank = smem + 2 * (TILE + 1);
     int32_t* s_cnt = smem + 3 * (TILE + 1);
+    __shared__ long long s_blockbase[MAX_COL_BLOCKS];
     const Seg S = ctx->segs[0];
     const int64_t np1 = S.n + 1;
     const int64_t m = S.m;
+    // rpB holds block-local offsets; block b starts after the entries of blocks < b
+    if (threadIdx.x == 0) {
+        long long acc = 0;
+        for (int b = 0; b < nb; ++b) {
+            s_blockbase[b] = acc;
+            acc += rpB[(int64_t)b * np1 + S.n];
+        }
+    }
+    __syncthreads();
     for (int64_t t = blockIdx.x; t < S.k2_ntiles; t += gridDim.x) {
         int64_t x0;
         int nfull, R, E, D;
@@ -460,7 +655,7 @@ __global__ void __launch_bounds__(K2_THREADS)
         for (int i = threadIdx.x; i < R * nb; i += blockDim.x) s_cnt[i] = 0;
         __syncthreads();
         // rank of every entry among the tile's entries of the same (row, block)
-        tile_walk<RP, ITEMS>(s_rowend, nfull, E, D, [&](int r, int y) {
+        tile_walk<RP, BUILD_ITEMS>(s_rowend, nfull, E, D, [&](int r, int y) {
             const int b = col_block(s_col[y], shift, nb);
             const int k = atomicAdd(&s_cnt[r * nb + b], 1);
             s_rank[y] = (k << 4) | b;  // nb <= 16
@@ -472,10 +667,11 @@ __global__ void __launch_bounds__(K2_THREADS)
             if (c) s_cnt[i] = atomicAdd(&cursor[(int64_t)(i % nb) * np1 + x0 + i / nb], c);
         }
         __syncthreads();
-        tile_walk<RP, ITEMS>(s_rowend, nfull, E, D, [&](int r, int y) {
+        tile_walk<RP, BUILD_ITEMS>(s_rowend, nfull, E, D, [&](int r, int y) {
             const int b = s_rank[y] & 15;
             const int64_t u = x0 + r;
-            const int64_t pos = (int64_t)rpB[(int64_t)b * np1 + u] + s_cnt[r * nb + b] + (s_rank[y] >> 4);
+            const int64_t pos =
+                s_blockbase[b] + (int64_t)rpB[(int64_t)b * np1 + u] + s_cnt[r * nb + b] + (s_rank[y] >> 4);
             if (pos >= 0 && pos < m) colB[pos] = s_col[y];
         });
         __syncthreads();
@@ -591,43 +787,71 @@ __global__ void k_setup_blocks(Ctx* ctx, const int32_t* rpB, const int32_t* colB
     }
     segs[0].k2_ntiles = 0;
     ctx->num_segs = nb + 1;
+    ctx->k2_tile = k2_tile;
 }
 
 // ---------------------------------------------------------------------------
 // K2: SpMV (select2nd, min) fused with the three hooks
 // ---------------------------------------------------------------------------
 
-template <int ITEMS>
+template <int THREADS, int ITEMS>
 constexpr int k2_smem_bytes() {
-    return (2 * (K2_THREADS * ITEMS + 1) + K2_THREADS * ITEMS) * (int)sizeof(int32_t);
+    return (2 * (THREADS * ITEMS + 1) + THREADS * ITEMS) * (int)sizeof(int32_t);
 }
 
-template <typename RP, int ITEMS>
-__global__ void __launch_bounds__(K2_THREADS)
-    k2_hook(Ctx* __restrict__ ctx, cudaGraphConditionalHandle cond, int use_cond) {
-    constexpr int TILE = K2_THREADS * ITEMS;
-    // The loop condition starts every iteration at "stop"; only the last CTA
-    // of k3_grandparent sets it back to "continue" when work remains, so a
-    // device loop can never outlive its iteration bookkeeping.
+// first kernel of every iteration: resets the loop condition to "stop" (only
+// the last CTA of k3_grandparent sets it back to "continue" when work
+// remains, so a device loop can never outlive its bookkeeping), and before a
+// full SpMV sets mngf to INF for every active graph
+__global__ void k_iter_begin(Ctx* __restrict__ ctx, cudaGraphConditionalHandle cond, int use_cond) {
     if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
+    if (ctx->mode != 0) return;
+    const int64_t total = ctx->k3_total;
+    for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
+        const Seg& S = ctx->segs[ctx->k3_tile_seg[t]];
+        if (!S.active) continue;
+        const int64_t v0 = (t - S.k3_tile0) * K3_TILE;
+        const int64_t v1 = min(v0 + K3_TILE, S.n);
+        for (int64_t v = v0 + threadIdx.x; v < v1; v += blockDim.x) S.mngf[v] = INF;
+    }
+}
+
+// a1, full iteration: mngf[u] = min_{v in N(u)} gf[v] -- the (select2nd,min)
+// SpMV of Section 4.1.  One CTA of THREADS threads handles one merge-path
+// tile of THREADS*ITEMS items (row ends + entries) at a time; a row split
+// over tiles (or over column blocks) contributes one partial minimum per
+// tile, merged by atomic min into mngf.
+//
+// block < 0: every tile of every segment (no column blocking).  block >= 0:
+// only the tiles of column block `block` of graph 0; the blocks of a graph
+// run as consecutive launches, so a row's minimum from this block can be
+// merged into mngf with a plain load-min-store.
+template <typename RP, int THREADS, int ITEMS>
+__global__ void __launch_bounds__(THREADS) k2_spmv(Ctx* __restrict__ ctx, int block) {
+    constexpr int TILE = THREADS * ITEMS;
+    if (ctx->mode != 0) return;
     extern __shared__ int32_t smem[];
     int32_t* s_rowend = smem;                 // local end offset of each row in the tile
     int32_t* s_mngf = smem + (TILE + 1);      // per-row minimum over the tile's entries
     int32_t* s_val = smem + 2 * (TILE + 1);   // gf[col_idx[e]] for the tile's entries
     const int tid = threadIdx.x;
-    const int64_t T = ctx->k2_total;
     const int32_t* __restrict__ tile_seg = ctx->k2_tile_seg;
     const int32_t* __restrict__ tile_row = ctx->k2_tile_row;
     const Seg* __restrict__ segs = ctx->segs;
+    int64_t t_begin = 0, T = ctx->k2_total;
+    if (block >= 0) {
+        if (block + 1 >= ctx->num_segs) return;
+        t_begin = segs[1 + block].k2_tile0;
+        T = t_begin + segs[1 + block].k2_ntiles;
+    }
+    const bool merge = block >= 0;
 
-    for (int64_t t = blockIdx.x; t < T; t += gridDim.x) {
+    for (int64_t t = t_begin + blockIdx.x; t < T; t += gridDim.x) {
         const Seg* S = segs + tile_seg[t];
         if (!segs[S->leader].active) continue;
         const RP* __restrict__ rp = (const RP*)S->rp;
-        const int32_t* __restrict__ ci = S->ci;
         const int32_t* __restrict__ gf = S->gf;
-        const int32_t* __restrict__ p = S->p;
-        int32_t* f = S->f;
+        int32_t* mngf = S->mngf;
         const int64_t n = S->n, m = S->m;
         const int64_t lt = t - S->k2_tile0;
         const int64_t d0 = lt * TILE;
@@ -640,12 +864,13 @@ __global__ void __launch_bounds__(K2_THREADS)
         const int R = nfull + (x1 < n ? 1 : 0);       // plus the row still open at the tile end
         const int E = (int)(y1 - y0);                 // entries in this tile
         const int D = (int)(d1 - d0);
+        const RP* __restrict__ rpt = rp + x0 + 1;     // row ends of the tile's rows
+        const int32_t* __restrict__ cit = S->ci + y0; // the tile's entries
 
         // phase 1: row ends, and the gathered grandparents of the tile's entries
-        for (int i = tid; i < R; i += K2_THREADS) {
-            int64_t e = rp_at(rp, x0 + i + 1);
-            e = e < y1 ? e : y1;
-            e -= y0;
+        for (int i = tid; i < R; i += THREADS) {
+            int64_t e = rp_at(rpt, i);
+            e = (e < y1 ? e : y1) - y0;
             s_rowend[i] = (int32_t)(e < 0 ? 0 : e);
             s_mngf[i] = INF;
         }
@@ -653,61 +878,155 @@ __global__ void __launch_bounds__(K2_THREADS)
             int32_t c[ITEMS];
 #pragma unroll
             for (int q = 0; q < ITEMS; ++q) {
-                int j = tid + q * K2_THREADS;
-                c[q] = j < E ? ld_stream(ci + y0 + j) : -1;
+                const int j = tid + q * THREADS;
+                c[q] = j < E ? ld_stream(cit + j) : -1;
             }
 #pragma unroll
             for (int q = 0; q < ITEMS; ++q) {
-                int j = tid + q * K2_THREADS;
+                const int j = tid + q * THREADS;
                 if (j < E) s_val[j] = ((uint32_t)c[q] < (uint64_t)n) ? __ldg(gf + c[q]) : INF;
             }
         }
         __syncthreads();
 
         // phase 2: every thread walks ITEMS consecutive merge-path items
-        // (row ends and entries) and min-reduces entries per row
+        // (row ends and entries) and min-reduces entries per row.  The walk
+        // keeps the open row's end in a register; it reads an entry only while
+        // y < that end <= E (or, for the row still open at the tile end, while
+        // items remain), so y stays inside the tile.
         const int k0 = tid * ITEMS;
+        int r = -1;
+        int32_t acc = INF;
         if (k0 < D) {
             int lo = 0, hi = nfull;
             while (lo < hi) {
-                int mid = (lo + hi) >> 1;
+                const int mid = (lo + hi) >> 1;
                 if (s_rowend[mid] + mid < k0)
                     lo = mid + 1;
                 else
                     hi = mid;
             }
-            int r = lo, y = k0 - lo;
-            int32_t acc = INF;
-            const int kend = min(k0 + ITEMS, D);
-            for (int k = k0; k < kend; ++k) {
-                if (r < nfull && y >= s_rowend[r]) {
+            r = lo;
+            int y = k0 - lo;
+            int rend = r < nfull ? s_rowend[r] : 0x7fffffff;
+            const int steps = min(ITEMS, D - k0);
+            for (int k = 0; k < steps; ++k) {
+                if (y >= rend) {
                     if (acc != INF) atomicMin(&s_mngf[r], acc);
                     acc = INF;
                     ++r;
+                    rend = r < nfull ? s_rowend[r] : 0x7fffffff;
                 } else {
-                    acc = min(acc, s_val[y < E ? y : E - 1]);
+                    acc = min(acc, s_val[y]);
                     ++y;
                 }
             }
-            if (acc != INF && r < R) atomicMin(&s_mngf[r], acc);
+        }
+        // the row still open at the end of each thread's items: when a whole
+        // warp ends inside one row (a hub), reduce in registers first
+        {
+            const int key = (acc != INF && r >= 0 && r < R) ? r : -1;
+            const int key0 = __shfl_sync(0xffffffffu, key, 0);
+            if (__all_sync(0xffffffffu, key == key0)) {
+                const int32_t wmin = (int32_t)__reduce_min_sync(0xffffffffu, (unsigned)acc);
+                if ((tid & 31) == 0 && key0 >= 0) atomicMin(&s_mngf[key0], wmin);
+            } else if (key >= 0) {
+                atomicMin(&s_mngf[key], acc);
+            }
         }
         __syncthreads();
 
-        // phase 3: hooks for every row with entries in this tile
-        for (int i = tid; i < R; i += K2_THREADS) {
+        // phase 3: the tile's row minima into mngf.  A row that starts and
+        // ends inside this tile has its complete minimum here: a plain store
+        // (or, for a column block, a plain load-min-store, since no other
+        // launch runs at the same time).  Only the first and last row of a
+        // tile can continue in a neighbouring tile; those merge by atomic min.
+        // (Atomic merges of every row measured 2.6x slower on this kernel.)
+        const bool first_whole = rp_at(rp, x0) >= y0;
+        for (int i = tid; i < R; i += THREADS) {
             const int32_t mn = s_mngf[i];
-            if (mn == INF) continue;
-            const int64_t u = x0 + i;
-            const int32_t g = gf[u];
-            const int32_t pu = p[u];
-            // stochastic hooking: f_next[f[u]] <-min mngf[u]; a no-op unless
-            // mngf[u] < gf[u] because f[p[u]] <= p[p[u]] = gf[u] throughout
-            if (mn < g) atomicMin(f + pu, mn);
-            // aggressive hooking and shortcutting: f_next[u] <-min mngf[u], gf[u]
-            const int32_t m2 = mn < g ? mn : g;
-            if (m2 < pu) atomicMin(f + u, m2);
+            const bool whole = i < nfull && (i > 0 || first_whole);
+            if (whole) {
+                if (!merge)
+                    mngf[x0 + i] = mn;
+                else if (mn < mngf[x0 + i])
+                    mngf[x0 + i] = mn;
+            } else if (mn != INF) {
+                atomicMin(mngf + x0 + i, mn);
+            }
         }
         __syncthreads();
+    }
+}
+
+// a1, sparse iteration (Section 4.2's SpMSpV): only vertices whose gf
+// changed in the last iteration can lower a neighbour's minimum, and gf never
+// increases, so min(old mngf, pushes of the new gf of changed vertices) is
+// exactly the SpMV of the new gf.  One warp per changed vertex.
+template <typename RP>
+__global__ void __launch_bounds__(256) k2_push(Ctx* __restrict__ ctx) {
+    if (ctx->mode != 1) return;
+    const Seg S = ctx->segs[0];
+    if (!S.active) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctx->sparse_iters++;
+    const RP* rp = (const RP*)S.rp;
+    const int32_t* __restrict__ F = ctx->frontier;
+    const unsigned len = ctx->frontier_len;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = warp; i < len; i += nwarps) {
+        const int32_t v = F[i];
+        if ((uint32_t)v >= (uint64_t)S.n) continue;
+        const int32_t g = S.gf[v];
+        int64_t b = rp_at(rp, v), e = rp_at(rp, v + 1);
+        if (b < 0) b = 0;
+        if (e > S.m) e = S.m;
+        for (int64_t k = b + lane; k < e; k += 32) {
+            const int32_t u = S.ci[k];
+            if ((uint32_t)u < (uint64_t)S.n) atomicMin(S.mngf + u, g);
+        }
+    }
+}
+
+// a2 + a3: hooks from mngf for every vertex of every active graph.
+//   stochastic hooking  f_next[f[u]] <-min mngf[u]  (a no-op unless mngf[u] <
+//                        gf[u], because f[p[u]] <= p[p[u]] = gf[u] throughout)
+//   aggressive hooking  f_next[u] <-min mngf[u]
+//   shortcutting        f_next[u] <-min gf[u]
+__global__ void __launch_bounds__(K3_THREADS) k2_hook(Ctx* __restrict__ ctx) {
+    const int64_t T = ctx->k3_total;
+    const int tid = threadIdx.x;
+    for (int64_t t = blockIdx.x; t < T; t += gridDim.x) {
+        const Seg* S = ctx->segs + ctx->k3_tile_seg[t];
+        if (!S->active) continue;
+        const int64_t n = S->n;
+        const int64_t v0 = (t - S->k3_tile0) * K3_TILE;
+        const int32_t* __restrict__ mngf = S->mngf;
+        const int32_t* __restrict__ gf = S->gf;
+        const int32_t* __restrict__ p = S->p;
+        int32_t* f = S->f;
+        int32_t mn[K3_ITEMS], g[K3_ITEMS], pu[K3_ITEMS];
+#pragma unroll
+        for (int q = 0; q < K3_ITEMS; ++q) {
+            const int64_t v = v0 + tid + q * K3_THREADS;
+            mn[q] = v < n ? mngf[v] : INF;
+        }
+#pragma unroll
+        for (int q = 0; q < K3_ITEMS; ++q) {
+            const int64_t v = v0 + tid + q * K3_THREADS;
+            const bool live = mn[q] != INF;
+            g[q] = live ? gf[v] : 0;
+            pu[q] = live ? p[v] : 0;
+        }
+#pragma unroll
+        for (int q = 0; q < K3_ITEMS; ++q) {
+            if (mn[q] == INF) continue;
+            const int64_t v = v0 + tid + q * K3_THREADS;
+            if (mn[q] < g[q]) atomicMin(f + pu[q], mn[q]);
+            const int32_t m2 = mn[q] < g[q] ? mn[q] : g[q];
+            if (m2 < pu[q]) atomicMin(f + v, m2);
+        }
     }
 }
 
@@ -743,16 +1062,31 @@ __device__ __forceinline__ void close_iteration(Ctx* ctx, cudaGraphConditionalHa
         int li = ctx->loop_iter + 1;
         ctx->loop_iter = li;
         ctx->any_active = any;
+        if (ctx->sparse_enabled) {
+            // next iteration: push from the vertices whose gf just changed
+            // when their rows are few enough, else a full SpMV
+            const unsigned len = ctx->frontier_next;
+            const unsigned long long deg = ctx->frontier_deg;
+            ctx->frontier_len = len;
+            ctx->frontier_next = 0;
+            ctx->frontier_deg = 0;
+            ctx->mode = (deg <= (unsigned long long)ctx->sparse_max_deg) ? 1 : 0;
+        }
         if (use_cond) cudaGraphSetConditional(cond, (any && li < ctx->loop_limit) ? 1u : 0u);
     }
 }
 
+template <typename RP>
 __global__ void __launch_bounds__(K3_THREADS)
     k3_grandparent(Ctx* __restrict__ ctx, cudaGraphConditionalHandle cond, int use_cond) {
     __shared__ int s_red[K3_THREADS / 32];
+    __shared__ int s_woff[K3_THREADS / 32];
+    __shared__ unsigned s_base;
     __shared__ int s_last;
     const int tid = threadIdx.x;
+    const int lane = tid & 31;
     const int64_t T = ctx->k3_total;
+    const bool track = ctx->sparse_enabled != 0;
     for (int64_t t = blockIdx.x; t < T; t += gridDim.x) {
         Seg* S = ctx->segs + ctx->k3_tile_seg[t];
         if (!S->active) continue;
@@ -761,32 +1095,65 @@ __global__ void __launch_bounds__(K3_THREADS)
         int32_t* f = S->f;
         int32_t* p = S->p;
         int32_t* gf = S->gf;
-        int32_t fu[K3_ITEMS];
+        // all loads of a thread first (f[v], gf[v], then the gathers f[f[v]])
+        int32_t fu[K3_ITEMS], old[K3_ITEMS], g[K3_ITEMS];
 #pragma unroll
         for (int q = 0; q < K3_ITEMS; ++q) {
-            int64_t v = v0 + tid + q * K3_THREADS;
+            const int64_t v = v0 + tid + q * K3_THREADS;
             fu[q] = v < n ? f[v] : 0;
+            old[q] = v < n ? gf[v] : 0;
         }
+#pragma unroll
+        for (int q = 0; q < K3_ITEMS; ++q) g[q] = f[fu[q]];
         int c = 0;
+        unsigned masks[K3_ITEMS];
 #pragma unroll
         for (int q = 0; q < K3_ITEMS; ++q) {
-            int64_t v = v0 + tid + q * K3_THREADS;
+            const int64_t v = v0 + tid + q * K3_THREADS;
+            const bool ch = v < n && g[q] != old[q];
             if (v < n) {
-                const int32_t g = f[fu[q]];
-                if (g != gf[v]) {
-                    gf[v] = g;
+                if (ch) {
+                    gf[v] = g[q];
                     ++c;
                 }
                 p[v] = fu[q];
             }
+            masks[q] = __ballot_sync(0xffffffffu, ch);
         }
-        c = __reduce_add_sync(0xffffffffu, c);
-        if ((tid & 31) == 0) s_red[tid >> 5] = c;
+        c = __reduce_add_sync(0xffffffffu, c);  // == popcounts of the masks, summed
+        if (lane == 0) s_red[tid >> 5] = c;
         __syncthreads();
-        if (tid < 32) {
-            int x = tid < K3_THREADS / 32 ? s_red[tid] : 0;
-            x = __reduce_add_sync(0xffffffffu, x);
-            if (tid == 0 && x) atomicAdd(&S->changed, (unsigned int)x);
+        if (tid == 0) {
+            // one reservation per tile in the next iteration's frontier
+            int total = 0;
+            for (int w = 0; w < K3_THREADS / 32; ++w) {
+                const int x = s_red[w];
+                s_woff[w] = total;
+                total += x;
+            }
+            if (total) atomicAdd(&S->changed, (unsigned int)total);
+            s_base = (track && total) ? atomicAdd(&ctx->frontier_next, (unsigned)total) : 0u;
+        }
+        __syncthreads();
+        if (track && c) {
+            // frontier of the next iteration: the changed vertices of this
+            // tile, and the sum of their degrees
+            const RP* rp = (const RP*)S->rp;
+            unsigned off = s_base + (unsigned)s_woff[tid >> 5];
+            unsigned long long dsum = 0;
+#pragma unroll
+            for (int q = 0; q < K3_ITEMS; ++q) {
+                const unsigned mask = masks[q];
+                if (mask >> lane & 1u) {
+                    const int64_t v = v0 + tid + q * K3_THREADS;
+                    ctx->frontier[off + __popc(mask & ((1u << lane) - 1u))] = (int32_t)v;
+                    dsum += (unsigned long long)(rp_at(rp, v + 1) - rp_at(rp, v));
+                }
+                off += (unsigned)__popc(mask);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) dsum += __shfl_down_sync(0xffffffffu, dsum, o);
+            if (lane == 0 && dsum) atomicAdd(&ctx->frontier_deg, dsum);
         }
         __syncthreads();
     }
@@ -839,6 +1206,7 @@ __global__ void k_finish(Ctx* ctx, int32_t* iters_out) {
         ctx->sum.converged = s_cv[0];
         ctx->sum.loop_iter = ctx->loop_iter;
         ctx->sum.num_active = s_act[0];
+        ctx->sum.sparse_iters = ctx->sparse_iters;
     }
 }
 

@@ -7,7 +7,6 @@
 namespace fsv {
 
 constexpr int32_t INF = 0x7fffffff;
-constexpr int K2_THREADS = 256;
 constexpr int K3_THREADS = 256;
 constexpr int K3_ITEMS = 8;
 constexpr int K3_TILE = K3_THREADS * K3_ITEMS;
@@ -38,6 +37,7 @@ struct Seg {
     int32_t leader;      // segment whose state governs this one: itself, or for a
                          // column block of a graph, the graph's own segment
     int32_t pad;
+    int32_t* mngf;       // per-row minimum of gf over neighbours, kept across iterations
 };
 
 struct Summary {
@@ -46,6 +46,8 @@ struct Summary {
     int32_t converged;      // AND over segments
     int32_t loop_iter;      // iterations the device loop executed in this call
     int32_t num_active;     // segments still active
+    int32_t sparse_iters;   // iterations that pushed from the frontier instead of a full SpMV
+    int32_t pad;
     unsigned long long trace[TRACE_LEN];  // segment 0: changed count per iteration
 };
 
@@ -64,6 +66,17 @@ struct Ctx {
     unsigned int k3_done;    // CTA ticket for the last-block epilogue
     int32_t any_active;
     int32_t val_status;      // validation result bits
+    // sparse iterations (single graph): vertices whose gf changed in the last
+    // iteration push their new gf to their neighbours' mngf instead of a full SpMV
+    int32_t sparse_enabled;
+    int32_t mode;                  // this iteration: 0 = full SpMV, 1 = push from the frontier
+    int32_t* frontier;             // vertices whose gf changed in the last iteration
+    unsigned int frontier_len;
+    unsigned int frontier_next;    // being filled by this iteration's k3
+    unsigned long long frontier_deg;   // sum of their degrees (being filled)
+    int64_t sparse_max_deg;        // push when the frontier's degree sum is at most this
+    int32_t sparse_iters;          // iterations run in push mode in this call
+    int32_t pad2;
     Summary sum;
 };
 

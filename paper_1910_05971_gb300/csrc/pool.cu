@@ -26,6 +26,7 @@ struct AdmitDesc {
     int32_t* f;
     int32_t* p;
     int32_t* gf;
+    int32_t* mngf;
     int64_t n, m;
     int32_t slot;
     int32_t pad;
@@ -67,6 +68,7 @@ __global__ void k_pool_admit(Ctx* ctx, Seg* segs, int32_t* k2_seg, int32_t* k2_r
         s.user = a.slot;
         s.leader = a.slot;
         s.pad = 0;
+        s.mngf = a.mngf;
         segs[a.slot] = s;
     }
     if (i == 0) {
@@ -81,6 +83,8 @@ __global__ void k_pool_admit(Ctx* ctx, Seg* segs, int32_t* k2_seg, int32_t* k2_r
         ctx->loop_iter = 0;
         ctx->k3_done = 0;
         ctx->val_status = 0;
+        ctx->sparse_enabled = 0;
+        ctx->mode = 0;
     }
 }
 
@@ -113,7 +117,7 @@ struct Pool {
 static size_t align_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
 
 static size_t region_bytes(int64_t n, int64_t m) {
-    return align_up((size_t)(n + 1) * 4) + align_up((size_t)(m > 0 ? m : 1) * 4) + 3 * align_up((size_t)n * 4);
+    return align_up((size_t)(n + 1) * 4) + align_up((size_t)(m > 0 ? m : 1) * 4) + 4 * align_up((size_t)n * 4);
 }
 
 static bool arena_alloc(Pool* P, size_t bytes, size_t* off) {
@@ -186,7 +190,7 @@ fastsv_status fastsv_pool_create(fastsv_t h, size_t budget, int32_t max_slots) {
     P->budget = budget / ALIGN * ALIGN;
     P->max_slots = max_slots;
     P->slots.resize(max_slots);
-    const int64_t tile = (int64_t)K2_THREADS * k2_items(h);
+    const int64_t tile = k2_tile(h);
     // every slot needs at least 4(n+m) bytes, so n + m <= budget / 4 over all slots
     const int64_t cap2 = (int64_t)(P->budget / 4) / tile + max_slots + 1;
     const int64_t cap3 = (int64_t)(P->budget / 16) / K3_TILE + max_slots + 1;
@@ -263,7 +267,7 @@ fastsv_status fastsv_pool_step(fastsv_t h, int32_t iters, void* stream) {
     Pool* P = h->pool;
     cudaStream_t s = (cudaStream_t)stream;
     const int items = k2_items(h);
-    const int32_t tile = K2_THREADS * items;
+    const int32_t tile = (int32_t)k2_tile(h);
     // the slot snapshot read below must be the previous step's final one
     if (P->stepped) FSV_CUDA(h, cudaEventSynchronize(P->step_done));
     size_t na = P->admitted.size();
@@ -293,6 +297,8 @@ fastsv_status fastsv_pool_step(fastsv_t h, int32_t iters, void* stream) {
             a.p = (int32_t*)(base + o);
             o += align_up((size_t)S.n * 4);
             a.gf = (int32_t*)(base + o);
+            o += align_up((size_t)S.n * 4);
+            a.mngf = (int32_t*)(base + o);
             a.n = S.n;
             a.m = S.m;
             a.slot = slot;
@@ -317,7 +323,7 @@ fastsv_status fastsv_pool_step(fastsv_t h, int32_t iters, void* stream) {
     if (any) {
         h->loop_limit_host = iters;
         const bool graph = h->opt.use_graph != 0;
-        fastsv_status st = run_loop(h, P->d_ctx, 0, items, s);
+        fastsv_status st = run_loop(h, P->d_ctx, 0, 0, items, 0, s);
         if (st != FASTSV_OK) return st;
         if (graph) {
             // the loop's iteration count is read back with the segment table

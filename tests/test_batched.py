@@ -84,4 +84,4 @@ def test_batched_config_full():
     ref_lab, ref_it = oracle_batch(batch)
     assert np.array_equal(lab, ref_lab)
     assert np.array_equal(iters, ref_it)
-    assert launches == 5 + 2 * int(ref_it.max())
+    assert launches == 5 + 5 * int(ref_it.max())

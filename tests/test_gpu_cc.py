@@ -73,11 +73,12 @@ def _ragged_graphs():
     return out
 
 
+@pytest.mark.parametrize("threads", [64, 256])
 @pytest.mark.parametrize("items", [4, 8, 16])
 @pytest.mark.parametrize("bits", [32, 64])
-def test_per_iteration_parity_ragged(items, bits):
+def test_per_iteration_parity_ragged(items, bits, threads):
     for rp, ci in _ragged_graphs():
-        per_iteration_parity(rp, ci, bits=bits, k2_items=items)
+        per_iteration_parity(rp, ci, bits=bits, k2_items=items, k2_threads=threads)
 
 
 @pytest.mark.parametrize("col_blocks", [2, 3, 4, 16])
@@ -85,9 +86,9 @@ def test_per_iteration_parity_column_blocks(col_blocks):
     """Column-blocked hooking (one pass per column range, partial minima
     hooked directly) reproduces Algorithm 2 iteration by iteration."""
     for bits in (32, 64):
-        for items in (4, 8):
+        for items, threads in ((4, 64), (8, 256), (16, 64)):
             for rp, ci in _ragged_graphs():
-                per_iteration_parity(rp, ci, bits=bits, k2_items=items, col_blocks=col_blocks)
+                per_iteration_parity(rp, ci, bits=bits, k2_items=items, k2_threads=threads, col_blocks=col_blocks)
 
 
 def test_column_blocks_with_unsorted_rows():
@@ -224,8 +225,8 @@ def test_non_default_stream_and_launch_count():
             lab = s.cc(rp_d, ci_d, stream=stream)
         stream.synchronize()
         assert np.array_equal(lab.cpu().numpy(), f)
-        # set-up (3) + finish (1) + two kernels per device-loop iteration
-        assert s.kernel_launches() == 4 + 2 * it
+        # set-up (3) + finish (1) + five kernels per device-loop iteration
+        assert s.kernel_launches() == 4 + 5 * it
 
 
 # ---------------------------------------------------------------------------
@@ -261,3 +262,35 @@ def test_rmat_s26_full():
     assert conv and np.array_equal(f, ref)
     assert st["iterations"] == it
     assert st["changed_per_iter"] == ch.tolist()[:64]
+
+
+# ---------------------------------------------------------------------------
+# sparse iterations (push from the vertices whose grandparent changed)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("sparse_div", [0, 1, 4, 1 << 20])
+def test_per_iteration_parity_sparse_modes(sparse_div):
+    """Iterations that push from the changed vertices instead of a full SpMV
+    (sparse_div = 1: every iteration after the first) still reproduce
+    Algorithm 2's pointer graph after every iteration."""
+    for rp, ci in _ragged_graphs():
+        per_iteration_parity(rp, ci, sparse_div=sparse_div)
+    for rp, ci in _ragged_graphs()[-3:]:
+        per_iteration_parity(rp, ci, sparse_div=sparse_div, col_blocks=4, bits=32)
+
+
+def test_sparse_iterations_are_used_and_exact():
+    # R-MAT: late frontiers are small, so the default threshold pushes
+    rp, ci = graphgen.rmat_s16()
+    f, it, _, ch = oracle.fastsv(rp, ci)
+    dense, st_d = gpu_solve(rp, ci, sparse_div=0, bits=32)
+    sparse, st_s = gpu_solve(rp, ci, bits=32)
+    assert st_d["sparse_iters"] == 0 and st_s["sparse_iters"] > 0
+    # lattice: frontiers stay large; forcing a push in every iteration after
+    # the first must still be exact
+    rpg, cig = graphgen.grid(300, 0.55, 100, seed=7)
+    fg, itg, _, chg = oracle.fastsv(rpg, cig)
+    always, st_a = gpu_solve(rpg, cig, sparse_div=1)
+    assert st_a["sparse_iters"] == itg - 1
+    for got, st, ref, n_it, trace in ((dense, st_d, f, it, ch), (sparse, st_s, f, it, ch), (always, st_a, fg, itg, chg)):
+        assert np.array_equal(got, ref) and st["iterations"] == n_it and st["changed_per_iter"] == trace.tolist()
