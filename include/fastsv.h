@@ -86,7 +86,7 @@ typedef struct {
     int32_t col_blocks;    /* column blocks of the SpMV for one large graph: 0 = automatic (currently: none)
                               1 = never, 2..16 = that many (each call then copies the CSR once into
                               column-block order; worth it only for graphs needing many iterations) */
-    int32_t k2_threads;    /* threads per CTA of the SpMV kernel: 64 (default) or 256 */
+    int32_t k2_threads;    /* threads per CTA of the SpMV kernel: 256 (default) or 64 */
     int32_t sparse_div;    /* single-graph calls: an iteration pushes from the vertices whose grandparent
                               changed (SpMSpV, Section 4.2) instead of a full SpMV when the degree sum of
                               those vertices is at most m / sparse_div (default 2); 0 = always full SpMV */

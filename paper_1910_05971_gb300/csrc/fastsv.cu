@@ -102,7 +102,7 @@ int k2_items(const fastsv_ctx* h) {
 
 int k2_threads(const fastsv_ctx* h) {
     int t = h->opt.k2_threads;
-    return (t == 64 || t == 256) ? t : 64;
+    return (t == 64 || t == 256) ? t : 256;
 }
 
 int64_t k2_tile(const fastsv_ctx* h) { return (int64_t)k2_threads(h) * k2_items(h); }
@@ -561,7 +561,7 @@ void fastsv_default_options(fastsv_options* o) {
     o->timing = 1;
     o->fail_alloc_after = 0;
     o->col_blocks = 0;
-    o->k2_threads = 64;
+    o->k2_threads = 256;
     o->sparse_div = 2;
 }
 
