@@ -228,6 +228,43 @@ fastsv_status fastsv_pool_poll(fastsv_t h, int32_t* done_slots, int32_t* done_it
 /* Pool occupancy: slots in use and bytes of the budget in use. */
 fastsv_status fastsv_pool_usage(fastsv_t h, int32_t* slots_used, size_t* bytes_used);
 
+/*
+ * Largest vertex count fastsv_cc_noalloc accepts (the size of its built-in
+ * scratch: two int32 vectors of this length, 8 MiB, plus a counter, held on
+ * every GPU that loads the library until the process exits).
+ */
+#define FASTSV_NOALLOC_MAX_VERTICES (1 << 20)
+
+/*
+ * Connected components of one graph without any device allocation by the
+ * library.  (The paper has no counterpart: this is a deployment variant of
+ * fastsv_cc.)  It is for callers that must not allocate device memory while
+ * they run: a host framework that has reserved all device memory in its own
+ * pool, where cudaMalloc would fail or fragment that pool; latency-critical
+ * loops that cannot afford cudaMalloc/cudaFree, which can synchronise the
+ * whole device; and code that may not call an allocator at all.  It needs no
+ * handle: the per-vertex state the solve keeps lives in a fixed scratch array
+ * built into the library instead of handle workspace.
+ *   n          vertices, 0 <= n <= FASTSV_NOALLOC_MAX_VERTICES; a larger n
+ *              returns FASTSV_ERR_UNSUPPORTED and does nothing
+ *   row_ptr    device int32[n+1], row_ptr[0] = 0 (symmetric CSR as for fastsv_cc)
+ *   col_idx    device int32[row_ptr[n]] (may be NULL when there are no entries)
+ *   labels_out device int32[n]: the smallest vertex id of each vertex's component
+ *   max_iters  iteration cap (>= 1); reaching it returns FASTSV_ERR_MAX_ITERS
+ *   iterations_out  host int32 or NULL: iterations executed
+ *   stream     cudaStream_t
+ * Calls no cudaMalloc, cudaFree or other allocating routine.  The first call
+ * on each device looks up the scratch array's device address (with that
+ * device current) and caches it; make that first call before any stream
+ * capture.  All calls on a device share the one scratch array, which keeps
+ * the previous call's contents (every call re-initialises what it reads):
+ * calls that overlap on the GPU, from any thread or stream, race on it and
+ * must be serialised by the caller.  Synchronises with `stream` once per
+ * iteration; returns when labels_out is final.
+ */
+fastsv_status fastsv_cc_noalloc(int64_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t* labels_out,
+                                int32_t max_iters, int32_t* iterations_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

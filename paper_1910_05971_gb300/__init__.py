@@ -24,7 +24,7 @@ from ._lib import (  # noqa: F401  (re-exported C names)
     fastsv_default_options, fastsv_create, fastsv_destroy, fastsv_cc, fastsv_cc_host, fastsv_cc_batched,
     fastsv_get_stats, fastsv_status_string, fastsv_last_cuda_error, fastsv_kernel_launches,
     fastsv_pool_create, fastsv_pool_bytes, fastsv_pool_add, fastsv_pool_step, fastsv_pool_poll,
-    fastsv_pool_usage, load, library_path,
+    fastsv_pool_usage, load, library_path, fastsv_cc_noalloc, FASTSV_NOALLOC_MAX_VERTICES,
 )
 
 

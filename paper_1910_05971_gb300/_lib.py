@@ -101,7 +101,11 @@ _SIGNATURES = [
     ("fastsv_pool_step", C.c_int, [_P, C.c_int32, _P]),
     ("fastsv_pool_poll", C.c_int, [_P, _P, _P, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     ("fastsv_pool_usage", C.c_int, [_P, C.POINTER(C.c_int32), C.POINTER(C.c_size_t)]),
+    ("fastsv_cc_noalloc", C.c_int, [C.c_int64, _P, _P, _P, C.c_int32, C.POINTER(C.c_int32), _P]),
 ]
+
+# largest vertex count of fastsv_cc_noalloc (FASTSV_NOALLOC_MAX_VERTICES)
+FASTSV_NOALLOC_MAX_VERTICES = 1 << 20
 
 
 def library_path() -> str:
@@ -222,3 +226,11 @@ def fastsv_pool_usage(h: int) -> tuple[int, int, int]:
     b = C.c_size_t(0)
     st = _call("fastsv_pool_usage", h, C.byref(used), C.byref(b))
     return st, used.value, b.value
+
+
+def fastsv_cc_noalloc(n: int, row_ptr: int, col_idx: int | None, labels_out: int, max_iters: int,
+                      stream: int) -> tuple[int, int]:
+    """Allocation-free solve (see include/fastsv.h): returns (status, iterations)."""
+    it = C.c_int32(0)
+    st = _call("fastsv_cc_noalloc", n, row_ptr, col_idx, labels_out, max_iters, C.byref(it), stream)
+    return st, it.value
