@@ -10,22 +10,37 @@
 //   f   the parent vector being updated (plays "f_next"); equal to p at the
 //       start of every iteration; every write is an atomic min
 //   gf  grandparents p[p] (Algorithm 3's gf), recomputed after each iteration
+//   mngf the per-row minimum of gf over the neighbours (Algorithm 3's mngf);
+//       kept from one iteration to the next, so an iteration that pushes
+//       only from changed vertices (Section 4.2) can update it in place
 //
-// One iteration = two kernels:
-//   k2_hook        mngf[u] = min_{v in N(u)} gf[v] (the (select2nd,min) SpMV),
-//                  then f[p[u]] min= mngf[u]          (stochastic hooking)
-//                  and  f[u] min= min(mngf[u], gf[u]) (aggressive hooking +
-//                  shortcutting).  Work is split by merge-path tiles over
-//                  (rows + entries), so every CTA gets the same amount of
-//                  work whatever the degree distribution, reads a contiguous
-//                  slice of col_idx, and a hub row simply spans several
-//                  tiles: each tile hooks with the minimum over its part of
-//                  the row, which is exact because every hook is a min.
+// One iteration = five kernels (graph nodes of one WHILE-loop body):
+//   k_iter_begin   clears the loop condition; resets mngf to +inf when the
+//                  coming iteration is a full SpMV
+//   k2_spmv        mngf[u] = min_{v in N(u)} gf[v] (the (select2nd,min)
+//                  SpMV of Algorithm 3).  Work is split by merge-path tiles
+//                  over (rows + entries), so every CTA gets the same amount
+//                  of work whatever the degree distribution and reads a
+//                  contiguous slice of col_idx; a hub row spans several
+//                  tiles, whose partial minima merge with an atomic min.
+//                  With column blocks, one launch per block of columns, so
+//                  the gathers of one launch hit a slice of gf that stays
+//                  in L2.
+//   k2_push        the sparse alternative (SpMSpV, Section 4.2): only the
+//                  vertices whose gf changed last iteration push their new
+//                  gf to their neighbours' mngf.  Exact because gf never
+//                  increases: the minimum over the unchanged neighbours is
+//                  already in mngf.
+//   k2_hook        f[p[u]] min= mngf[u]          (stochastic hooking)
+//                  f[u] min= min(mngf[u], gf[u]) (aggressive hooking +
+//                  shortcutting)
 //   k3_grandparent gf'[u] = f[f[u]], count gf' != gf (the termination test of
 //                  Section 3.4 / Algorithm 3's ISNE + reduce), gf = gf',
-//                  p = f.  The last CTA to finish advances every segment's
-//                  iteration counter, retires segments whose count is zero,
-//                  and sets the CUDA-graph WHILE condition.
+//                  p = f, and collect the changed vertices as the next
+//                  frontier.  The last CTA to finish advances every
+//                  segment's iteration counter, retires segments whose count
+//                  is zero, picks the next iteration's mode (full SpMV or
+//                  push) and sets the CUDA-graph WHILE condition.
 // Because hooks are atomic mins of values that depend only on (p, gf), the
 // result of an iteration does not depend on thread scheduling: the device
 // reproduces the sequential pointer graph of Algorithm 2 bit for bit.

@@ -44,6 +44,13 @@ class PoolBackend:
         self._iters = np.zeros(max_slots, dtype=np.int32)
         self._stream = torch.cuda.Stream()
 
+    def host_buffer(self, n: int) -> np.ndarray:
+        """int32 host buffer for a graph's labels, in pinned memory so that the
+        device-to-host copy of a harvest runs at full link speed (torch's
+        pinned-memory cache makes reuse cheap)."""
+        import torch
+        return torch.empty(max(n, 1), dtype=torch.int32).pin_memory().numpy()
+
     def bytes_for(self, n: int, m: int) -> int:
         return _lib.fastsv_pool_bytes(n, m)
 
@@ -78,10 +85,11 @@ class PoolBackend:
 class Request:
     __slots__ = ("rp", "ci", "labels", "future", "t_submit", "t_admit", "t_done", "slot", "iterations")
 
-    def __init__(self, rp, ci):
+    def __init__(self, rp, ci, host_buffer=None):
         self.rp = np.ascontiguousarray(rp, dtype=np.int32)
         self.ci = np.ascontiguousarray(ci, dtype=np.int32)
-        self.labels = np.empty(max(len(self.rp) - 1, 1), dtype=np.int32)
+        n = max(len(self.rp) - 1, 1)
+        self.labels = host_buffer(n) if host_buffer is not None else np.empty(n, dtype=np.int32)
         self.future: Future = Future()
         self.t_submit = time.perf_counter()
         self.t_admit = None
@@ -110,7 +118,7 @@ class Server:
 
     # -- client side ------------------------------------------------------
     def submit(self, rp, ci) -> Future:
-        req = Request(rp, ci)
+        req = Request(rp, ci, getattr(self.backend, "host_buffer", None))
         n = len(req.rp) - 1
         if self.backend.bytes_for(n, len(req.ci)) > self.backend.budget:
             req.future.set_exception(ValueError("graph larger than the pool's HBM budget"))
