@@ -11,6 +11,10 @@ The arithmetic lives in ``oracle.c`` (plain C, compiled with gcc):
 * ``fastsv(..., form="alg3")``  Algorithm 3 (Section 4.1), the GraphBLAS form.
 * ``fastsv(..., form="omp")``   Algorithm 2 with OpenMP loops and atomic min;
   identical per iteration to the sequential form.
+* ``fastsv(..., form="sv1".."sv5")``  the convergence ablation of Section 5:
+  Algorithm 1 (Section 2), then grandparent hooking (3.1), stochastic hooking
+  (3.2), aggressive hooking with Algorithm 2's single-pass body (3.3) and early
+  termination (3.4) added one at a time; sv5 is Algorithm 2.
 * ``uf`` / ``bfs``  the exact result: every vertex labelled with the smallest
   vertex id of its connected component (the converged state, Section 3.4).
 
@@ -64,6 +68,10 @@ def _load(mutant: int = 0) -> C.CDLL:
             fn = getattr(lib, name)
             fn.argtypes = [i64, p, p, p, i64, p, i64, p]
             fn.restype = i64
+        lib.oracle_fastsv_sv.argtypes = [i64, p, p, p, i32, i64, p, i64, p]
+        lib.oracle_fastsv_sv.restype = i64
+        lib.oracle_sv_iteration.argtypes = [i64, p, p, p, p, p, i32]
+        lib.oracle_sv_iteration.restype = i64
         lib.oracle_fastsv_omp.argtypes = [i64, p, p, p, i64, p, i64, p, i32]
         lib.oracle_fastsv_omp.restype = i64
         lib.oracle_alg2_iteration.argtypes = [i64, p, p, p, p, p]
@@ -92,7 +100,9 @@ def fastsv(rp, ci, max_iters: int = 0, form: str = "alg2", nthreads: int = 0, tr
     last iteration (equal to the labels on convergence), the number of
     iterations executed, whether the last one found f[f] unchanged, and the
     per-iteration count of changed grandparents.  ``max_iters`` <= 0 runs to
-    convergence.
+    convergence.  ``form="sv1"`` .. ``"sv5"`` runs the convergence ablation of
+    Section 5 (Algorithm 1 plus the optimizations of Sections 3.1-3.4 one at a
+    time; sv5 is Algorithm 2); for sv1..sv4 the trace counts changed f.
     """
     n, rp, ci = _csr(rp, ci)
     lib = _load(mutant)
@@ -107,6 +117,9 @@ def fastsv(rp, ci, max_iters: int = 0, form: str = "alg2", nthreads: int = 0, tr
         it = lib.oracle_fastsv_alg3(*args)
     elif form == "omp":
         it = lib.oracle_fastsv_omp(*args, nthreads)
+    elif form in ("sv1", "sv2", "sv3", "sv4", "sv5"):
+        it = lib.oracle_fastsv_sv(n, rp.ctypes.data, ci.ctypes.data, f.ctypes.data, int(form[2]), max_iters,
+                                  trace.ctypes.data, trace_cap, conv.ctypes.data)
     else:
         raise ValueError(form)
     return f[:n], int(it), bool(conv[0]), trace[:min(it, trace_cap)].copy()
@@ -123,6 +136,19 @@ def iteration(rp, ci, f, mutant: int = 0) -> int:
     gp = np.empty(n, dtype=np.int32)
     return int(_load(mutant).oracle_alg2_iteration(n, rp.ctypes.data, ci.ctypes.data, f.ctypes.data,
                                                    fn.ctypes.data, gp.ctypes.data))
+
+
+def sv_iteration(rp, ci, f, variant: int, mutant: int = 0) -> int:
+    """Apply one iteration of ablation variant sv1..sv4 to ``f`` in place;
+    return the number of entries of f that changed."""
+    n, rp, ci = _csr(rp, ci)
+    assert f.dtype == np.int32 and f.flags.c_contiguous and len(f) == n and 1 <= variant <= 4
+    if n == 0:
+        return 0
+    fn = np.empty(n, dtype=np.int32)
+    fs = np.empty(n, dtype=np.int32)
+    return int(_load(mutant).oracle_sv_iteration(n, rp.ctypes.data, ci.ctypes.data, f.ctypes.data,
+                                                 fn.ctypes.data, fs.ctypes.data, variant))
 
 
 def uf(rp, ci) -> np.ndarray:

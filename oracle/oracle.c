@@ -17,6 +17,9 @@
  *                        GraphBLAS operations (mxv on (select2nd,min) with MIN
  *                        accumulation, assign with MIN, two eWiseMult MIN,
  *                        extractTuples + extract, ISNE + reduce(+), dup).
+ *   oracle_fastsv_sv     the convergence ablation sv1..sv5 of Section 5:
+ *                        Algorithm 1, then the optimizations of Sections
+ *                        3.1-3.4 added one at a time (sv5 = Algorithm 2).
  *   oracle_fastsv_omp    Algorithm 2 again with OpenMP parallel loops; every
  *                        min-update is an atomic min, so each iteration gives
  *                        exactly the sequential result.  Used for timing and
@@ -141,6 +144,108 @@ int64_t oracle_fastsv_alg2(int64_t n, const int64_t* rp, const int32_t* ci, int3
     *converged = (changed == 0);
     free(fnext);
     free(gfp);
+    return it;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Convergence ablation sv1..sv5 (Section 3, Section 5 "Speed of            */
+/* convergence"): Algorithm 1 with the optimizations of Section 3 added     */
+/* one at a time, in the order of Sections 3.1-3.4                          */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * One iteration of variant sv<variant>, 1 <= variant <= 4 (sv5 is Algorithm 2
+ * itself, oracle_fastsv_alg2).
+ *   sv1  Algorithm 1: tree hooking f_next[f[u]] <- f[v] for every (u,v) in E
+ *        whose f[u] is a root (f[u] == f[f[u]]) and f[v] < f[u]; f <- f_next;
+ *        then shortcutting f_next[u] <- f[f[u]] where f[u] != f[f[u]];
+ *        f <- f_next.  Several edges may write the same f_next[f[u]]: the
+ *        smallest value is kept, which makes the iteration deterministic.
+ *   sv2  sv1 hooking onto the grandparent f[f[v]] instead of f[v] (3.1).
+ *   sv3  sv2 without the root test f[u] == f[f[u]]: stochastic hooking (3.2).
+ *   sv4  the loop body of Algorithm 2: stochastic and aggressive hooking and
+ *        shortcutting, all from the same f (3.3), still stopping when f is
+ *        unchanged; sv5 adds the early termination of 3.4.
+ *   f      parent vector, replaced by the iteration's result
+ *   fnext  scratch of n entries;  fstart scratch of n entries
+ * Returns the number of u whose f[u] changed over the iteration (Algorithm 1
+ * stops when this is zero).
+ */
+int64_t oracle_sv_iteration(int64_t n, const int64_t* rp, const int32_t* ci, int32_t* f, int32_t* fnext,
+                            int32_t* fstart, int variant) {
+    memcpy(fstart, f, (size_t)n * sizeof(int32_t));
+    memcpy(fnext, f, (size_t)n * sizeof(int32_t));
+    if (variant <= 3) {
+        /* Step 1: tree hooking */
+        for (int64_t u = 0; u < n; ++u) {
+            const int32_t fu = f[u];
+#if MUTANT == 6 /* drop the root test of sv1/sv2 */
+            const int root = 1;
+#else
+            const int root = (fu == f[fu]);
+#endif
+            if (variant <= 2 && !root) continue;
+            for (int64_t e = rp[u]; e < rp[u + 1]; ++e) {
+                const int32_t v = ci[e];
+                const int32_t hv = variant == 1 ? f[v] : f[f[v]];
+                if (hv < fu) fnext[fu] = min32(fnext[fu], hv);
+            }
+        }
+        memcpy(f, fnext, (size_t)n * sizeof(int32_t));
+        /* Step 2: shortcutting, on the hooked pointer graph */
+        for (int64_t u = 0; u < n; ++u) {
+#if MUTANT == 7 /* shortcut from the pointer graph before hooking */
+            const int32_t gu = fstart[fstart[u]];
+#else
+            const int32_t gu = f[f[u]];
+#endif
+            if (f[u] != gu) fnext[u] = gu;
+        }
+        memcpy(f, fnext, (size_t)n * sizeof(int32_t));
+    } else {
+        /* the three steps of Algorithm 2, all reading the same f */
+        for (int64_t u = 0; u < n; ++u)
+            for (int64_t e = rp[u]; e < rp[u + 1]; ++e) {
+                const int32_t ffv = f[f[ci[e]]];
+                fnext[f[u]] = min32(fnext[f[u]], ffv); /* stochastic hooking */
+                fnext[u] = min32(fnext[u], ffv);       /* aggressive hooking */
+            }
+        for (int64_t u = 0; u < n; ++u) fnext[u] = min32(fnext[u], f[f[u]]); /* shortcutting */
+        memcpy(f, fnext, (size_t)n * sizeof(int32_t));
+    }
+    /* until f remains unchanged */
+    int64_t changed = 0;
+    for (int64_t u = 0; u < n; ++u) changed += (f[u] != fstart[u]);
+    return changed;
+}
+
+/*
+ * Variant sv<variant> (1..5) from f[u] = u until its stopping test holds, or
+ * max_iters iterations (<= 0: no limit).  Same arguments and return as
+ * oracle_fastsv_alg2; the trace holds the per-iteration count of the
+ * variant's own test (changed f for sv1..sv4, changed f[f] for sv5).
+ */
+int64_t oracle_fastsv_sv(int64_t n, const int64_t* rp, const int32_t* ci, int32_t* f, int variant,
+                         int64_t max_iters, int64_t* changed_trace, int64_t trace_cap, int32_t* converged) {
+    if (variant == 5) return oracle_fastsv_alg2(n, rp, ci, f, max_iters, changed_trace, trace_cap, converged);
+    *converged = 1;
+    if (n <= 0) return 0;
+    if (variant < 1 || variant > 5) {
+        *converged = 0;
+        return -1;
+    }
+    int32_t* fnext = (int32_t*)malloc((size_t)n * sizeof(int32_t));
+    int32_t* fstart = (int32_t*)malloc((size_t)n * sizeof(int32_t));
+    for (int64_t u = 0; u < n; ++u) f[u] = (int32_t)u;
+    int64_t it = 0, changed;
+    do {
+        changed = oracle_sv_iteration(n, rp, ci, f, fnext, fstart, variant);
+        if (changed_trace && it < trace_cap) changed_trace[it] = changed;
+        ++it;
+    } while (changed != 0 && (max_iters <= 0 || it < max_iters));
+    *converged = (changed == 0);
+    free(fnext);
+    free(fstart);
     return it;
 }
 
