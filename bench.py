@@ -186,9 +186,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--col-blocks", type=int, default=0)
-    ap.add_argument("--mode", default="single", choices=["single", "batched", "serve"],
+    ap.add_argument("--mode", default="single", choices=["single", "batched", "serve", "variants"],
                     help="single: one large graph (default, the headline); batched: 4096 ER graphs in one "
-                         "launch vs per-graph launches; serve: replay of the request trace")
+                         "launch vs per-graph launches; serve: replay of the request trace; variants: "
+                         "iterations and time of the convergence ablation sv1..sv5 and the asynchronous mode")
+    ap.add_argument("--variant-workloads", default="rmat_s16,grid_4096_p055_iso1M,rmat_s26_perm",
+                    help="variants mode: comma-separated workloads")
     ap.add_argument("--graphs", type=int, default=4096, help="batched mode: number of graphs")
     ap.add_argument("--requests", type=int, default=256, help="serve mode: trace prefix length")
     args = ap.parse_args()
@@ -207,6 +210,9 @@ def main():
     if args.mode == "serve":
         from paper_1910_05971_gb300 import benchmarks as bench_modes
         return bench_modes.run_serve(args, rank, world, local_rank)
+    if args.mode == "variants":
+        from paper_1910_05971_gb300 import benchmarks as bench_modes
+        return bench_modes.run_variants(args, rank, world, local_rank)
 
     import torch
     import paper_1910_05971_gb300 as fsv

@@ -60,12 +60,18 @@ typedef enum {
     FASTSV_ERR_FULL = 8           /* pool: no slot or not enough budget for the request right now */
 } fastsv_status;
 
-/* Solver variants.  FASTSV_MODE_SYNC is Algorithm 2 exactly: every update of
+/* Solver modes.  FASTSV_MODE_SYNC is Algorithm 2 exactly: every update of
  * an iteration reads the vectors as they were at its start (the f / f_next
  * separation of Section 2.4), so the pointer graph after iteration i is the
  * same on every run and equal to the CPU oracle's.  FASTSV_MODE_ASYNC reads
- * and writes one vector in place (the concurrent variant Section 2.4
- * mentions): labels are the same, iteration counts may differ. */
+ * and writes one parent vector in place (the concurrent variant Section 2.4
+ * mentions): one fused kernel per iteration hooks f[f[u]] and f[u] onto the
+ * row minimum of the live f[v] and shortcuts f[u] to f[f[u]]; the loop stops
+ * after an iteration that lowered no entry of f.  Labels are the same as in
+ * FASTSV_MODE_SYNC; the iteration count and changed_per_iter (rows whose
+ * processing lowered some entry) depend on the schedule.  Single-graph calls
+ * only: fastsv_cc_batched and fastsv_pool_create return
+ * FASTSV_ERR_UNSUPPORTED on an asynchronous handle. */
 enum { FASTSV_MODE_SYNC = 0, FASTSV_MODE_ASYNC = 1 };
 
 typedef struct {
@@ -90,7 +96,14 @@ typedef struct {
     int32_t sparse_div;    /* single-graph calls: an iteration pushes from the vertices whose grandparent
                               changed (SpMSpV, Section 4.2) instead of a full SpMV when the degree sum of
                               those vertices is at most m / sparse_div (default 2); 0 = always full SpMV */
-    int32_t reserved[3];
+    int32_t variant;       /* 0 (default) or 5: FastSV, Algorithm 2.  1..4: the convergence ablation of
+                              Section 5.2 -- 1 = Algorithm 1 (simplified SV, Section 2.4), 2 = + hooking
+                              to the grandparent (3.1), 3 = + stochastic hooking (3.2), 4 = Algorithm 2's
+                              loop body with aggressive hooking (3.3) but stopping when f is unchanged
+                              (no early termination, 3.4).  Variants 1..4 are deterministic per iteration,
+                              run a host loop (one synchronisation per iteration), single-graph calls in
+                              FASTSV_MODE_SYNC only; changed_per_iter then counts changed entries of f */
+    int32_t reserved[2];
 } fastsv_options;
 
 typedef struct {
@@ -227,6 +240,45 @@ fastsv_status fastsv_pool_poll(fastsv_t h, int32_t* done_slots, int32_t* done_it
 
 /* Pool occupancy: slots in use and bytes of the budget in use. */
 fastsv_status fastsv_pool_usage(fastsv_t h, int32_t* slots_used, size_t* bytes_used);
+
+/*
+ * Checkpoint and eviction (serving under memory pressure).  Between two
+ * steps a slot holds Algorithm 2's state at an iteration boundary: the parent
+ * vector f, the grandparents gf = f[f] and its iteration count (the snapshot
+ * p equals f there, and the pool runs no sparse iterations, so nothing else
+ * carries over).  fastsv_pool_evict copies that state into a host checkpoint
+ * and frees the slot and its pool memory; fastsv_pool_restore admits the
+ * graph again from the checkpoint, and the restored slot runs exactly the
+ * iterations it would have run without the interruption: same labels, same
+ * iteration count.
+ */
+
+/* Bytes of the checkpoint of a graph with n vertices (a 64-byte header, f, gf). */
+size_t fastsv_pool_checkpoint_bytes(int64_t n);
+
+/*
+ * Evict `slot`: waits for the last step, copies the slot's state into
+ * checkpoint_host (fastsv_pool_checkpoint_bytes(n) bytes of host memory,
+ * owned by the caller, pinned recommended), takes the slot out of the device
+ * loop and frees it and its pool memory.  The host buffers given when the
+ * graph was added are no longer referenced.  Synchronises.
+ * Errors: FASTSV_ERR_INVALID_ARG if `slot` is not a graph that has taken part
+ * in a step and is still iterating (a finished graph is harvested by
+ * fastsv_pool_poll; one added since the last step has no state yet).
+ */
+fastsv_status fastsv_pool_evict(fastsv_t h, int32_t slot, void* checkpoint_host);
+
+/*
+ * Admit a graph again from its checkpoint: arguments as fastsv_pool_add (the
+ * same graph; its host buffers must stay valid until it is harvested) plus
+ * the checkpoint.  The copies are enqueued on the pool's copy stream, so
+ * checkpoint_host, like the graph's buffers, must stay valid until the slot
+ * is harvested or evicted again.
+ * Errors: as fastsv_pool_add; FASTSV_ERR_INVALID_ARG also for a checkpoint
+ * whose header does not match (n, m) or is not a checkpoint.
+ */
+fastsv_status fastsv_pool_restore(fastsv_t h, int64_t n, const int32_t* row_ptr_host, const int32_t* col_idx_host,
+                                  int32_t* labels_host, const void* checkpoint_host, int32_t* slot_out);
 
 /*
  * Largest vertex count fastsv_cc_noalloc accepts (the size of its built-in

@@ -11,8 +11,8 @@ The arithmetic lives in ``oracle.c`` (plain C, compiled with gcc):
 * ``fastsv(..., form="alg3")``  Algorithm 3 (Section 4.1), the GraphBLAS form.
 * ``fastsv(..., form="omp")``   Algorithm 2 with OpenMP loops and atomic min;
   identical per iteration to the sequential form.
-* ``fastsv(..., form="sv1".."sv5")``  the convergence ablation of Section 5:
-  Algorithm 1 (Section 2), then grandparent hooking (3.1), stochastic hooking
+* ``fastsv(..., form="sv1".."sv5")``  the convergence ablation of Section 5.2:
+  Algorithm 1 (Section 2.4), then grandparent hooking (3.1), stochastic hooking
   (3.2), aggressive hooking with Algorithm 2's single-pass body (3.3) and early
   termination (3.4) added one at a time; sv5 is Algorithm 2.
 * ``uf`` / ``bfs``  the exact result: every vertex labelled with the smallest
@@ -101,7 +101,7 @@ def fastsv(rp, ci, max_iters: int = 0, form: str = "alg2", nthreads: int = 0, tr
     iterations executed, whether the last one found f[f] unchanged, and the
     per-iteration count of changed grandparents.  ``max_iters`` <= 0 runs to
     convergence.  ``form="sv1"`` .. ``"sv5"`` runs the convergence ablation of
-    Section 5 (Algorithm 1 plus the optimizations of Sections 3.1-3.4 one at a
+    Section 5.2 (Algorithm 1 plus the optimizations of Sections 3.1-3.4 one at a
     time; sv5 is Algorithm 2); for sv1..sv4 the trace counts changed f.
     """
     n, rp, ci = _csr(rp, ci)

@@ -17,7 +17,7 @@
  *                        GraphBLAS operations (mxv on (select2nd,min) with MIN
  *                        accumulation, assign with MIN, two eWiseMult MIN,
  *                        extractTuples + extract, ISNE + reduce(+), dup).
- *   oracle_fastsv_sv     the convergence ablation sv1..sv5 of Section 5:
+ *   oracle_fastsv_sv     the convergence ablation sv1..sv5 of Section 5.2:
  *                        Algorithm 1, then the optimizations of Sections
  *                        3.1-3.4 added one at a time (sv5 = Algorithm 2).
  *   oracle_fastsv_omp    Algorithm 2 again with OpenMP parallel loops; every
@@ -148,7 +148,7 @@ int64_t oracle_fastsv_alg2(int64_t n, const int64_t* rp, const int32_t* ci, int3
 }
 
 /* ---------------------------------------------------------------------- */
-/* Convergence ablation sv1..sv5 (Section 3, Section 5 "Speed of            */
+/* Convergence ablation sv1..sv5 (Section 3, Section 5.2 "Speed of          */
 /* convergence"): Algorithm 1 with the optimizations of Section 3 added     */
 /* one at a time, in the order of Sections 3.1-3.4                          */
 /* ---------------------------------------------------------------------- */

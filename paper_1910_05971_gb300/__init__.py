@@ -25,6 +25,7 @@ from ._lib import (  # noqa: F401  (re-exported C names)
     fastsv_get_stats, fastsv_status_string, fastsv_last_cuda_error, fastsv_kernel_launches,
     fastsv_pool_create, fastsv_pool_bytes, fastsv_pool_add, fastsv_pool_step, fastsv_pool_poll,
     fastsv_pool_usage, load, library_path, fastsv_cc_noalloc, FASTSV_NOALLOC_MAX_VERTICES,
+    fastsv_pool_checkpoint_bytes, fastsv_pool_evict, fastsv_pool_restore,
 )
 
 
@@ -54,7 +55,7 @@ class FastSV:
     def __init__(self, rowptr_bits: int = 64, mode: int = FASTSV_MODE_SYNC, max_iters: int = 4096,
                  validate: int = 0, use_graph: bool = True, k2_items: int = 8, grid_ctas_per_sm: int = 0,
                  l2_persist: bool = False, timing: bool = True, fail_alloc_after: int = 0, col_blocks: int = 0,
-                 k2_threads: int = 256, sparse_div: int = 2):
+                 k2_threads: int = 256, sparse_div: int = 2, variant: int = 0):
         _torch()
         o = fastsv_default_options()
         o.rowptr_bits = rowptr_bits
@@ -70,6 +71,7 @@ class FastSV:
         o.col_blocks = col_blocks
         o.k2_threads = k2_threads
         o.sparse_div = sparse_div
+        o.variant = variant
         self.options = o
         self.h = fastsv_create(o)
 

@@ -48,7 +48,8 @@ class fastsv_options(C.Structure):
         ("col_blocks", C.c_int32),
         ("k2_threads", C.c_int32),
         ("sparse_div", C.c_int32),
-        ("reserved", C.c_int32 * 3),
+        ("variant", C.c_int32),
+        ("reserved", C.c_int32 * 2),
     ]
 
 
@@ -101,6 +102,9 @@ _SIGNATURES = [
     ("fastsv_pool_step", C.c_int, [_P, C.c_int32, _P]),
     ("fastsv_pool_poll", C.c_int, [_P, _P, _P, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     ("fastsv_pool_usage", C.c_int, [_P, C.POINTER(C.c_int32), C.POINTER(C.c_size_t)]),
+    ("fastsv_pool_checkpoint_bytes", C.c_size_t, [C.c_int64]),
+    ("fastsv_pool_evict", C.c_int, [_P, C.c_int32, _P]),
+    ("fastsv_pool_restore", C.c_int, [_P, C.c_int64, _P, _P, _P, _P, C.POINTER(C.c_int32)]),
     ("fastsv_cc_noalloc", C.c_int, [C.c_int64, _P, _P, _P, C.c_int32, C.POINTER(C.c_int32), _P]),
 ]
 
@@ -226,6 +230,22 @@ def fastsv_pool_usage(h: int) -> tuple[int, int, int]:
     b = C.c_size_t(0)
     st = _call("fastsv_pool_usage", h, C.byref(used), C.byref(b))
     return st, used.value, b.value
+
+
+def fastsv_pool_checkpoint_bytes(n: int) -> int:
+    return _call("fastsv_pool_checkpoint_bytes", n)
+
+
+def fastsv_pool_evict(h: int, slot: int, checkpoint_host: int) -> int:
+    return _call("fastsv_pool_evict", h, slot, checkpoint_host)
+
+
+def fastsv_pool_restore(h: int, n: int, row_ptr_host: int, col_idx_host: int | None, labels_host: int | None,
+                        checkpoint_host: int) -> tuple[int, int]:
+    slot = C.c_int32(-1)
+    st = _call("fastsv_pool_restore", h, n, row_ptr_host, col_idx_host, labels_host, checkpoint_host,
+               C.byref(slot))
+    return st, slot.value
 
 
 def fastsv_cc_noalloc(n: int, row_ptr: int, col_idx: int | None, labels_out: int, max_iters: int,

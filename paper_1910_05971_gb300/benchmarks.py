@@ -212,3 +212,67 @@ def run_serve(args, rank, world, local_rank):
                                      "p99_ms": float(np.percentile(base_lat, 99) * 1e3)},
         "identical_labels_and_iterations": bool(same), "gpu_launches": int(launches), "clocks": clocks}),
         flush=True)
+
+
+def run_variants(args, rank, world, local_rank):
+    """Iterations and device time of every solver variant on the same graph:
+    the convergence ablation sv1..sv5 of Section 5.2 (Algorithm 1, then the
+    optimizations of Sections 3.1-3.4 one at a time; sv5 is the default
+    FastSV iteration) and the asynchronous mode.  Every variant must return
+    the same labels.  One JSON line per workload."""
+    import torch
+
+    import graphgen
+    import paper_1910_05971_gb300 as fsv
+
+    if rank != 0:
+        return  # one graph on one GPU; replicas would only repeat it
+    torch.cuda.set_device(local_rank)
+    names = args.variant_workloads.split(",")
+    stream = torch.cuda.current_stream()
+    for name in names:
+        t0 = time.time()
+        rp, ci = graphgen.WORKLOADS[name]()
+        n, m = len(rp) - 1, len(ci)
+        bits = 64 if m > np.iinfo(np.int32).max else 32
+        rp_d = torch.from_numpy(rp.astype(np.int64 if bits == 64 else np.int32)).cuda()
+        ci_d = torch.from_numpy(ci).cuda()
+        del rp, ci
+        _log(f"[bench] {name}: n={n} m={m} generated in {time.time() - t0:.1f}s")
+        labels = torch.empty(n, dtype=torch.int32, device="cuda")
+        ref = None
+        out = {}
+        configs = [(f"sv{v}", dict(variant=v)) for v in (1, 2, 3, 4, 5)]
+        configs.append(("async", dict(mode=fsv.FASTSV_MODE_ASYNC)))
+        for key, kw in configs:
+            s = fsv.FastSV(rowptr_bits=bits, max_iters=100000, **kw)
+            s.cc(rp_d, ci_d, labels)  # untimed: first launches, workspace
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            its = []
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(args.steps):
+                s.cc(rp_d, ci_d, labels, check_status=False)
+                its.append(s.stats()["iterations"])
+            e1.record(stream)
+            torch.cuda.synchronize()
+            st = s.stats()
+            s.close()
+            ms = e0.elapsed_time(e1) / args.steps
+            if ref is None:
+                ref = labels.clone()
+            same = bool(torch.equal(labels, ref))
+            out[key] = {"iterations": its[-1], "iterations_all_steps": sorted(set(its)), "ms_per_solve": ms,
+                        "gteps": m / (ms * 1e-3) / 1e9, "converged": bool(st["converged"]),
+                        "labels_equal_sv1": same,
+                        "loop": "device graph" if key in ("sv5", "async") else "host loop"}
+        red = 1.0 - out["sv5"]["iterations"] / max(out["sv1"]["iterations"], 1)
+        print(json.dumps({
+            "metric": "iterations and time per solver variant (convergence ablation, Section 5.2)",
+            "workload": name, "n": n, "m_directed": m, "steps": args.steps, "dtype": "int32",
+            "data": "synthetic", "variants": out, "iteration_reduction_sv5_vs_sv1": red,
+            "all_labels_equal": all(v["labels_equal_sv1"] for v in out.values()),
+        }), flush=True)
+        del rp_d, ci_d, labels, ref
+        torch.cuda.empty_cache()

@@ -18,6 +18,7 @@
 
 #include "fastsv_internal.h"
 #include "fastsv_kernels.cuh"
+#include "variants.cuh"
 
 using namespace fsv;
 
@@ -327,6 +328,158 @@ fastsv_status run_loop(fastsv_ctx* h, Ctx* ctx, int rp64_orig, int rp64_dense, i
     return rc;
 }
 
+// ---------------------------------------------------------------------------
+// convergence ablation sv1..sv4: host loop, one synchronisation per iteration
+// ---------------------------------------------------------------------------
+
+static fastsv_status run_variant_loop(fastsv_ctx* h, Ctx* ctx, int rp64, int items, int variant, int64_t n,
+                                      int32_t* f, cudaStream_t s) {
+    IterKernels K;
+    fastsv_status st = iter_kernels(h, rp64, rp64, items, &K);
+    if (st != FASTSV_OK) return st;
+    const int threads = k2_threads(h);
+    const int vgrid = h->num_sms * 8;
+    VarPtrs P{f, h->d_p, h->d_gf, h->d_mngf, &h->d_segs[0].changed, n};
+    const int root_test = variant <= 2, aggressive = variant == 4, two_phase = variant <= 3;
+    cudaEvent_t e[3];
+    for (int i = 0; i < 3; ++i) FSV_CUDA(h, cudaEventCreate(&e[i]));
+    float t_spmv = 0.f, t_rest = 0.f;
+    int iters = 0;
+    cudaGraphConditionalHandle none = 0;
+    int no_cond = 0, blk = -1;
+    fastsv_status rc = FASTSV_OK;
+    for (;;) {
+        void* a_begin[] = {(void*)&ctx, (void*)&none, (void*)&no_cond};
+        void* a_spmv[] = {(void*)&ctx, (void*)&blk};
+        void* a_hook[] = {(void*)&P, (void*)&root_test, (void*)&aggressive};
+        void* a_p[] = {(void*)&P};
+        void* a_commit[] = {(void*)&P, (void*)&two_phase};
+        void* a_close[] = {(void*)&ctx, (void*)&none, (void*)&no_cond};
+        int launched = 0;
+        cudaError_t ce = cudaEventRecord(e[0], s);
+        if (ce == cudaSuccess)
+            ce = cudaLaunchKernel((const void*)k_iter_begin, dim3(K.vtx_grid), dim3(256), a_begin, 0, s), ++launched;
+        if (ce == cudaSuccess)
+            ce = cudaLaunchKernel(K.spmv, dim3(K.spmv_grid), dim3(threads), a_spmv, K.spmv_smem, s), ++launched;
+        if (ce == cudaSuccess) ce = cudaEventRecord(e[1], s);
+        if (ce == cudaSuccess)
+            ce = cudaLaunchKernel((const void*)kv_hook, dim3(vgrid), dim3(256), a_hook, 0, s), ++launched;
+        if (ce == cudaSuccess && two_phase)
+            ce = cudaLaunchKernel((const void*)kv_shortcut, dim3(vgrid), dim3(256), a_p, 0, s), ++launched;
+        if (ce == cudaSuccess)
+            ce = cudaLaunchKernel((const void*)kv_commit, dim3(vgrid), dim3(256), a_commit, 0, s), ++launched;
+        if (ce == cudaSuccess)
+            ce = cudaLaunchKernel((const void*)kv_grand, dim3(vgrid), dim3(256), a_p, 0, s), ++launched;
+        if (ce == cudaSuccess)
+            ce = cudaLaunchKernel((const void*)k_close, dim3(1), dim3(256), a_close, 0, s), ++launched;
+        if (ce == cudaSuccess) ce = cudaEventRecord(e[2], s);
+        if (ce == cudaSuccess)
+            ce = cudaMemcpyAsync(h->h_scalar, &ctx->any_active, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+        h->launches += launched;
+        if (ce != cudaSuccess) {
+            rc = cuda_fail(h, ce);
+            break;
+        }
+        float a = 0.f, b = 0.f;
+        cudaEventElapsedTime(&a, e[0], e[1]);
+        cudaEventElapsedTime(&b, e[1], e[2]);
+        t_spmv += a;
+        t_rest += b;
+        ++iters;
+        if (((int32_t*)h->h_scalar)[0] == 0 || iters >= h->loop_limit_host) break;
+    }
+    for (int i = 0; i < 3; ++i) cudaEventDestroy(e[i]);
+    h->ms_k2 = t_spmv;
+    h->ms_hook = t_rest;
+    h->dense_iters = iters;
+    h->pending_loop_kernels = 0;
+    return rc;
+}
+
+// ---------------------------------------------------------------------------
+// asynchronous mode: {k_async, k_close} per iteration, in a device WHILE loop
+// (or a host loop when use_graph = 0)
+// ---------------------------------------------------------------------------
+
+constexpr int ASYNC_THREADS = 256, ASYNC_ITEMS = 8;
+
+static const void* async_func(int rp64) {
+    return rp64 ? (const void*)k_async<int64_t, ASYNC_THREADS, ASYNC_ITEMS>
+                : (const void*)k_async<int32_t, ASYNC_THREADS, ASYNC_ITEMS>;
+}
+
+static fastsv_status run_async_loop(fastsv_ctx* h, Ctx* ctx, int rp64, cudaStream_t s) {
+    const void* fn = async_func(rp64);
+    const int smem = k2_smem_bytes<ASYNC_THREADS, ASYNC_ITEMS>();
+    FSV_CUDA(h, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    int per_sm = 0;
+    FSV_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, ASYNC_THREADS, smem));
+    if (per_sm < 1) per_sm = 1;
+    if (h->opt.grid_ctas_per_sm > 0 && h->opt.grid_ctas_per_sm < per_sm) per_sm = h->opt.grid_ctas_per_sm;
+    const int grid = per_sm * h->num_sms;
+    if (h->opt.use_graph) {
+        GraphKey key{rp64 * 2 + rp64, ASYNC_ITEMS * 1000 + ASYNC_THREADS, FASTSV_MODE_ASYNC * 64, ctx};
+        auto it = h->graphs.find(key);
+        if (it == h->graphs.end()) {
+            LoopGraph lg;
+            FSV_CUDA(h, cudaGraphCreate(&lg.graph, 0));
+            FSV_CUDA(h, cudaGraphConditionalHandleCreate(&lg.cond, lg.graph, 1, cudaGraphCondAssignDefault));
+            alignas(cudaGraphNodeParams) unsigned char cp_storage[sizeof(cudaGraphNodeParams)];
+            memset(cp_storage, 0, sizeof(cp_storage));
+            cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(cp_storage);
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = lg.cond;
+            cp.conditional.type = cudaGraphCondTypeWhile;
+            cp.conditional.size = 1;
+            cudaGraphNode_t cond_node;
+            FSV_CUDA(h, cudaGraphAddNode(&cond_node, lg.graph, nullptr, nullptr, 0, &cp));
+            cudaGraph_t body = cp.conditional.phGraph_out[0];
+            cudaGraphConditionalHandle cond = lg.cond;
+            int use_cond = 1;
+            void* a_async[] = {(void*)&ctx};
+            void* a_close[] = {(void*)&ctx, (void*)&cond, (void*)&use_cond};
+            cudaKernelNodeParams kp;
+            memset(&kp, 0, sizeof(kp));
+            kp.func = (void*)fn;
+            kp.gridDim = dim3((unsigned)grid);
+            kp.blockDim = dim3(ASYNC_THREADS);
+            kp.sharedMemBytes = (unsigned)smem;
+            kp.kernelParams = a_async;
+            cudaGraphNode_t n1, n2;
+            FSV_CUDA(h, cudaGraphAddKernelNode(&n1, body, nullptr, 0, &kp));
+            memset(&kp, 0, sizeof(kp));
+            kp.func = (void*)k_close;
+            kp.gridDim = dim3(1);
+            kp.blockDim = dim3(256);
+            kp.kernelParams = a_close;
+            FSV_CUDA(h, cudaGraphAddKernelNode(&n2, body, &n1, 1, &kp));
+            FSV_CUDA(h, cudaGraphInstantiate(&lg.exec, lg.graph, 0));
+            it = h->graphs.emplace(key, lg).first;
+        }
+        FSV_CUDA(h, cudaGraphLaunch(it->second.exec, s));
+        h->pending_loop_kernels = 2;
+        return FASTSV_OK;
+    }
+    cudaGraphConditionalHandle none = 0;
+    int no_cond = 0, iters = 0;
+    for (;;) {
+        void* a_async[] = {(void*)&ctx};
+        void* a_close[] = {(void*)&ctx, (void*)&none, (void*)&no_cond};
+        cudaError_t ce = cudaLaunchKernel(fn, dim3(grid), dim3(ASYNC_THREADS), a_async, smem, s);
+        if (ce == cudaSuccess) ce = cudaLaunchKernel((const void*)k_close, dim3(1), dim3(256), a_close, 0, s);
+        if (ce == cudaSuccess)
+            ce = cudaMemcpyAsync(h->h_scalar, &ctx->any_active, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+        if (ce != cudaSuccess) return cuda_fail(h, ce);
+        h->launches += 2;
+        ++iters;
+        if (((int32_t*)h->h_scalar)[0] == 0 || iters >= h->loop_limit_host) break;
+    }
+    h->pending_loop_kernels = 0;
+    return FASTSV_OK;
+}
+
 int setup_grid(const fastsv_ctx* h) { return h->num_sms * 8; }
 
 // prefix sums of tile counts, merge-path partition, identity state of
@@ -476,8 +629,13 @@ static fastsv_status solve_single(fastsv_ctx* h, int64_t n, int64_t m, const voi
                                   int32_t* labels, cudaStream_t s) {
     const int rp64 = h->opt.rowptr_bits == 64;
     const int items = k2_items(h);
-    const int64_t tile = k2_tile(h);
-    const int nb = m > 0 ? choose_col_blocks(h, n, m) : 1;
+    // the ablation variants sv1..sv4 and the asynchronous mode run unblocked
+    // and without sparse iterations
+    const int variant = (h->opt.variant >= 1 && h->opt.variant <= 4) ? h->opt.variant : 0;
+    const bool async = h->opt.mode == FASTSV_MODE_ASYNC;
+    const bool plain = variant == 0 && !async;
+    const int64_t tile = async ? (int64_t)ASYNC_THREADS * ASYNC_ITEMS : k2_tile(h);
+    const int nb = (m > 0 && plain) ? choose_col_blocks(h, n, m) : 1;
     int shift = 0;
     while (shift < 31 && ((int64_t)nb << shift) < n) ++shift;
     const int nb_eff = nb > 1 ? (int)((n + (1ll << shift) - 1) >> shift) : 1;
@@ -500,10 +658,10 @@ static fastsv_status solve_single(fastsv_ctx* h, int64_t n, int64_t m, const voi
     prm.ci = ci;
     prm.f = labels;
     prm.p = h->d_p;
-    prm.gf = h->d_gf;
+    prm.gf = variant == 1 ? h->d_p : h->d_gf;  // sv1's SpMV gathers parents, not grandparents
     prm.mngf = h->d_mngf;
     prm.frontier = h->d_frontier;
-    prm.sparse_max_deg = h->opt.sparse_div > 0 ? m / h->opt.sparse_div : -1;
+    prm.sparse_max_deg = (plain && h->opt.sparse_div > 0) ? m / h->opt.sparse_div : -1;
     prm.n = n;
     prm.m = m;
     prm.k2_tile = (int32_t)tile0;
@@ -532,10 +690,20 @@ static fastsv_status solve_single(fastsv_ctx* h, int64_t n, int64_t m, const voi
     }
     k_init_state<<<setup_grid(h), 256, 0, s>>>(h->d_ctx);
     h->pending_fixed_launches += 1;
+    if (variant == 1) {
+        kv_iota<<<setup_grid(h), 256, 0, s>>>(h->d_gf, n);  // grandparents for the root test
+        h->pending_fixed_launches += 1;
+    }
     FSV_CUDA(h, cudaGetLastError());
     FSV_CUDA(h, cudaEventRecord(h->ev_setup, s));
     h->loop_limit_host = prm.loop_limit;
-    if ((st = run_loop(h, h->d_ctx, rp64, loop_rp64, items, nb_eff > 1 ? nb_eff : 0, s)) != FASTSV_OK) return st;
+    if (variant)
+        st = run_variant_loop(h, h->d_ctx, rp64, items, variant, n, labels, s);
+    else if (async)
+        st = run_async_loop(h, h->d_ctx, rp64, s);
+    else
+        st = run_loop(h, h->d_ctx, rp64, loop_rp64, items, nb_eff > 1 ? nb_eff : 0, s);
+    if (st != FASTSV_OK) return st;
     return finish_call(h, s, nullptr, n, m, true);
 }
 
@@ -592,7 +760,8 @@ fastsv_status fastsv_create(fastsv_t* out, const fastsv_options* opt) {
     if (o.mode != FASTSV_MODE_SYNC && o.mode != FASTSV_MODE_ASYNC) return FASTSV_ERR_INVALID_ARG;
     if (o.max_iters < 1 || o.max_iters > (1 << 30)) return FASTSV_ERR_INVALID_ARG;
     if (o.validate < 0 || o.validate > 2) return FASTSV_ERR_INVALID_ARG;
-    if (o.mode == FASTSV_MODE_ASYNC) return FASTSV_ERR_UNSUPPORTED;
+    if (o.variant < 0 || o.variant > 5) return FASTSV_ERR_INVALID_ARG;
+    if (o.mode == FASTSV_MODE_ASYNC && o.variant >= 1 && o.variant <= 4) return FASTSV_ERR_INVALID_ARG;
     fastsv_ctx* h = new fastsv_ctx();
     h->opt = o;
     fastsv_status st = FASTSV_OK;
@@ -725,6 +894,8 @@ fastsv_status fastsv_cc_batched(fastsv_t h, int32_t G, const int64_t* vtx_off, c
         return FASTSV_OK;
     }
     if (!vtx_off || !edge_off || !row_ptr || !labels_out) return FASTSV_ERR_INVALID_ARG;
+    if (h->opt.mode != FASTSV_MODE_SYNC || (h->opt.variant >= 1 && h->opt.variant <= 4))
+        return FASTSV_ERR_UNSUPPORTED;  // the ablation and the asynchronous mode are single-graph only
     cudaStream_t s = (cudaStream_t)stream;
     order_after_previous(h, s);
     FSV_CUDA(h, cudaMemcpyAsync(h->h_scalar, vtx_off + G, 8, cudaMemcpyDeviceToHost, s));

@@ -29,7 +29,7 @@ struct AdmitDesc {
     int32_t* mngf;
     int64_t n, m;
     int32_t slot;
-    int32_t pad;
+    int32_t iters0;  // iterations already run (a graph restored from a checkpoint), else 0
 };
 
 struct AdmitBatch {
@@ -61,7 +61,7 @@ __global__ void k_pool_admit(Ctx* ctx, Seg* segs, int32_t* k2_seg, int32_t* k2_r
         s.k2_ntiles = (a.m > 0 && a.n > 0) ? (int32_t)((a.n + a.m + b.k2_tile - 1) / b.k2_tile) : 0;
         s.k3_ntiles = (int32_t)((a.n + K3_TILE - 1) / K3_TILE);
         s.active = a.n > 0;
-        s.iters = 0;
+        s.iters = a.iters0;  // > 0 keeps the restored f, p, gf (k_init_state skips the slot)
         s.status = 0;
         s.converged = a.n == 0;
         s.changed = 0;
@@ -93,7 +93,22 @@ struct Slot {
     int64_t n = 0, m = 0;
     size_t off = 0, bytes = 0;
     int32_t* labels_host = nullptr;
+    int32_t iters0 = 0;  // iterations run before a restore
 };
+
+// host checkpoint of one graph at an iteration boundary: header, f[n], gf[n]
+constexpr uint32_t CKPT_MAGIC = 0x46535643u;  // "FSVC"
+constexpr uint32_t CKPT_VERSION = 1;
+constexpr size_t CKPT_HEADER = 64;
+struct CkptHeader {
+    uint32_t magic, version;
+    int64_t n, m;
+    int32_t iters, status;
+};
+static_assert(sizeof(CkptHeader) <= CKPT_HEADER, "checkpoint header");
+
+// offsets of the vectors inside a slot's region: rp, ci, f, p, gf, mngf
+static size_t off_f(int64_t n, int64_t m);
 
 struct Pool {
     Ctx* d_ctx = nullptr;
@@ -119,6 +134,11 @@ static size_t align_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
 static size_t region_bytes(int64_t n, int64_t m) {
     return align_up((size_t)(n + 1) * 4) + align_up((size_t)(m > 0 ? m : 1) * 4) + 4 * align_up((size_t)n * 4);
 }
+static size_t off_f(int64_t n, int64_t m) {
+    return align_up((size_t)(n + 1) * 4) + align_up((size_t)(m > 0 ? m : 1) * 4);
+}
+static size_t off_p(int64_t n, int64_t m) { return off_f(n, m) + align_up((size_t)n * 4); }
+static size_t off_gf(int64_t n, int64_t m) { return off_p(n, m) + align_up((size_t)n * 4); }
 
 static bool arena_alloc(Pool* P, size_t bytes, size_t* off) {
     for (auto it = P->free_list.begin(); it != P->free_list.end(); ++it) {
@@ -185,6 +205,8 @@ size_t fastsv_pool_bytes(int64_t n, int64_t m) {
 fastsv_status fastsv_pool_create(fastsv_t h, size_t budget, int32_t max_slots) {
     if (!h || budget < ALIGN || max_slots < 1 || max_slots > (1 << 20)) return FASTSV_ERR_INVALID_ARG;
     if (h->pool) return FASTSV_ERR_INVALID_ARG;
+    if (h->opt.mode != FASTSV_MODE_SYNC || (h->opt.variant >= 1 && h->opt.variant <= 4))
+        return FASTSV_ERR_UNSUPPORTED;  // the pool runs the default iteration only
     Pool* P = new Pool();
     h->pool = P;
     P->budget = budget / ALIGN * ALIGN;
@@ -221,14 +243,28 @@ fastsv_status fastsv_pool_create(fastsv_t h, size_t budget, int32_t max_slots) {
     return FASTSV_OK;
 }
 
-fastsv_status fastsv_pool_add(fastsv_t h, int64_t n, const int32_t* rp, const int32_t* ci, int32_t* labels_host,
-                              int32_t* slot_out) {
+}  // extern "C"
+
+namespace fsv {
+
+// admit a graph: a slot, an arena region, the copies of its CSR (and, for a
+// restore, of its checkpointed f -> f and p, gf -> gf) on the copy stream
+static fastsv_status admit(fastsv_t h, int64_t n, const int32_t* rp, const int32_t* ci, int32_t* labels_host,
+                           const unsigned char* ckpt, int32_t* slot_out) {
     if (!h || !h->pool || !slot_out || n < 0 || n > (int64_t)INT32_MAX) return FASTSV_ERR_INVALID_ARG;
     if (!rp || (n > 0 && !labels_host)) return FASTSV_ERR_INVALID_ARG;
     Pool* P = h->pool;
     *slot_out = -1;
     const int64_t m = rp[n];
     if (m < 0 || (m > 0 && !ci)) return FASTSV_ERR_INVALID_ARG;
+    int32_t iters0 = 0;
+    if (ckpt) {
+        CkptHeader hd;
+        memcpy(&hd, ckpt, sizeof(hd));
+        if (hd.magic != CKPT_MAGIC || hd.version != CKPT_VERSION || hd.n != n || hd.m != m || hd.iters < 1)
+            return FASTSV_ERR_INVALID_ARG;
+        iters0 = hd.iters;
+    }
     const size_t bytes = region_bytes(n, m);
     if (bytes > P->budget) return FASTSV_ERR_INVALID_ARG;  // can never fit
     int slot = -1;
@@ -247,11 +283,21 @@ fastsv_status fastsv_pool_add(fastsv_t h, int64_t n, const int32_t* rp, const in
     S.off = off;
     S.bytes = bytes;
     S.labels_host = labels_host;
+    S.iters0 = iters0;
     char* base = P->arena + off;
     cudaError_t e = cudaMemcpyAsync(base, rp, (size_t)(n + 1) * 4, cudaMemcpyHostToDevice, P->copy_stream);
     if (e == cudaSuccess && m > 0)
         e = cudaMemcpyAsync(base + align_up((size_t)(n + 1) * 4), ci, (size_t)m * 4, cudaMemcpyHostToDevice,
                             P->copy_stream);
+    if (e == cudaSuccess && ckpt && n > 0) {
+        const unsigned char* fh = ckpt + CKPT_HEADER;
+        const unsigned char* gh = fh + (size_t)n * 4;
+        e = cudaMemcpyAsync(base + off_f(n, m), fh, (size_t)n * 4, cudaMemcpyHostToDevice, P->copy_stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(base + off_p(n, m), fh, (size_t)n * 4, cudaMemcpyHostToDevice, P->copy_stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(base + off_gf(n, m), gh, (size_t)n * 4, cudaMemcpyHostToDevice, P->copy_stream);
+    }
     if (e != cudaSuccess) {
         arena_free(P, off, bytes);
         S = Slot();
@@ -260,6 +306,75 @@ fastsv_status fastsv_pool_add(fastsv_t h, int64_t n, const int32_t* rp, const in
     P->admitted.push_back(slot);
     *slot_out = slot;
     return FASTSV_OK;
+}
+
+// the last step has finished: its device loop's kernels are counted
+static fastsv_status settle_step(fastsv_t h, Pool* P) {
+    if (!P->stepped) return FASTSV_OK;
+    cudaError_t e = cudaEventSynchronize(P->step_done);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    if (h->pool_loop_pending) {
+        h->launches += (int64_t)h->pending_loop_kernels * *(int32_t*)(h->h_scalar + 2);
+        h->pool_loop_pending = false;
+    }
+    return FASTSV_OK;
+}
+
+}  // namespace fsv
+
+extern "C" {
+
+fastsv_status fastsv_pool_add(fastsv_t h, int64_t n, const int32_t* rp, const int32_t* ci, int32_t* labels_host,
+                              int32_t* slot_out) {
+    return admit(h, n, rp, ci, labels_host, nullptr, slot_out);
+}
+
+size_t fastsv_pool_checkpoint_bytes(int64_t n) {
+    if (n < 0) return 0;
+    return CKPT_HEADER + 8 * (size_t)n;
+}
+
+fastsv_status fastsv_pool_evict(fastsv_t h, int32_t slot, void* checkpoint_host) {
+    if (!h || !h->pool || !checkpoint_host) return FASTSV_ERR_INVALID_ARG;
+    Pool* P = h->pool;
+    if (slot < 0 || slot >= P->max_slots || P->slots[slot].state != 2) return FASTSV_ERR_INVALID_ARG;
+    fastsv_status st = settle_step(h, P);
+    if (st != FASTSV_OK) return st;
+    Slot& S = P->slots[slot];
+    const Seg& D = P->h_segs[slot];
+    if (!D.active || S.n == 0) return FASTSV_ERR_INVALID_ARG;  // finished: harvest it with fastsv_pool_poll
+    CkptHeader hd;
+    memset(&hd, 0, sizeof(hd));
+    hd.magic = CKPT_MAGIC;
+    hd.version = CKPT_VERSION;
+    hd.n = S.n;
+    hd.m = S.m;
+    hd.iters = D.iters;
+    hd.status = D.status;
+    unsigned char* out = (unsigned char*)checkpoint_host;
+    memset(out, 0, CKPT_HEADER);
+    memcpy(out, &hd, sizeof(hd));
+    const char* base = P->arena + S.off;
+    cudaError_t e = cudaMemcpyAsync(out + CKPT_HEADER, base + off_f(S.n, S.m), (size_t)S.n * 4,
+                                    cudaMemcpyDeviceToHost, P->copy_stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out + CKPT_HEADER + (size_t)S.n * 4, base + off_gf(S.n, S.m), (size_t)S.n * 4,
+                            cudaMemcpyDeviceToHost, P->copy_stream);
+    // the slot leaves the device loop: no later step may touch its region
+    if (e == cudaSuccess) e = cudaMemsetAsync(&P->d_segs[slot].active, 0, sizeof(int32_t), P->copy_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(P->copy_stream);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    P->h_segs[slot].active = 0;
+    P->dirty = true;  // its tiles leave the lists at the next step
+    arena_free(P, S.off, S.bytes);
+    S = Slot();
+    return FASTSV_OK;
+}
+
+fastsv_status fastsv_pool_restore(fastsv_t h, int64_t n, const int32_t* rp, const int32_t* ci, int32_t* labels_host,
+                                  const void* checkpoint_host, int32_t* slot_out) {
+    if (!checkpoint_host) return FASTSV_ERR_INVALID_ARG;
+    return admit(h, n, rp, ci, labels_host, (const unsigned char*)checkpoint_host, slot_out);
 }
 
 fastsv_status fastsv_pool_step(fastsv_t h, int32_t iters, void* stream) {
@@ -302,6 +417,7 @@ fastsv_status fastsv_pool_step(fastsv_t h, int32_t iters, void* stream) {
             a.n = S.n;
             a.m = S.m;
             a.slot = slot;
+            a.iters0 = S.iters0;
             S.state = 2;
         }
         k_pool_admit<<<1, ADMIT_MAX, 0, s>>>(P->d_ctx, P->d_segs, P->d_k2_seg, P->d_k2_row, P->d_k3_seg, b);
@@ -343,14 +459,8 @@ fastsv_status fastsv_pool_poll(fastsv_t h, int32_t* done_slots, int32_t* done_it
     if (!h || !h->pool || !n_done || cap < 0 || (cap > 0 && !done_slots)) return FASTSV_ERR_INVALID_ARG;
     Pool* P = h->pool;
     *n_done = 0;
-    if (P->stepped) {
-        cudaError_t e = cudaEventSynchronize(P->step_done);
-        if (e != cudaSuccess) return cuda_fail(h, e);
-        if (h->pool_loop_pending) {
-            h->launches += 2 * (int64_t) * (int32_t*)(h->h_scalar + 2);
-            h->pool_loop_pending = false;
-        }
-    }
+    fastsv_status sst = settle_step(h, P);
+    if (sst != FASTSV_OK) return sst;
     int nd = 0, act = 0;
     std::vector<int> harvested;
     for (int i = 0; i < P->max_slots; ++i) {

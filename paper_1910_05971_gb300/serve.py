@@ -11,6 +11,12 @@ Requests (CSR graphs in host memory) arrive on any thread through
      paper) -- their labels are copied to host memory and their slot and
      memory are freed for the next admissions.
 
+Optional preemption under memory pressure (``preempt_after_steps``): when
+the request at the head of the queue has not fitted for that many steps, the
+largest resident graph that has run at least as long is checkpointed to host
+memory (its f, f[f] and iteration count) and freed, and queued right behind
+the head; restored later, it resumes exactly where it stopped.
+
 Graphs admitted while others are on the device join the running batch at the
 next iteration boundary; each graph's iteration sequence depends only on its
 own edges, so its labels and iteration count are the same alone and in any
@@ -43,6 +49,7 @@ class PoolBackend:
         self._done = np.zeros(max_slots, dtype=np.int32)
         self._iters = np.zeros(max_slots, dtype=np.int32)
         self._stream = torch.cuda.Stream()
+        self._n: dict[int, int] = {}  # vertices of the graph in each occupied slot
 
     def host_buffer(self, n: int) -> np.ndarray:
         """int32 host buffer for a graph's labels, in pinned memory so that the
@@ -62,6 +69,7 @@ class PoolBackend:
         if st == _lib.FASTSV_ERR_FULL:
             return None
         _lib.check(st, "fastsv_pool_add")
+        self._n[slot] = n
         return slot
 
     def step(self, iters: int):
@@ -75,6 +83,33 @@ class PoolBackend:
         _lib.check(st, "fastsv_pool_poll")
         return [(int(self._done[i]), int(self._iters[i])) for i in range(nd)], na
 
+    def evict(self, slot: int) -> np.ndarray:
+        """Checkpoint a still-iterating slot to host memory and free it
+        (fastsv_pool_evict).  Returns the checkpoint."""
+        n = self.slot_vertices(slot)
+        buf = self._pinned_bytes(_lib.fastsv_pool_checkpoint_bytes(n))
+        _lib.check(_lib.fastsv_pool_evict(self.h, slot, buf.ctypes.data), "fastsv_pool_evict")
+        return buf
+
+    def restore(self, rp: np.ndarray, ci: np.ndarray, labels: np.ndarray, checkpoint: np.ndarray):
+        """Admit a graph again from its checkpoint; a slot id, or None if the
+        pool is full right now."""
+        n = len(rp) - 1
+        st, slot = _lib.fastsv_pool_restore(self.h, n, rp.ctypes.data, ci.ctypes.data if len(ci) else None,
+                                            labels.ctypes.data if n > 0 else None, checkpoint.ctypes.data)
+        if st == _lib.FASTSV_ERR_FULL:
+            return None
+        _lib.check(st, "fastsv_pool_restore")
+        self._n[slot] = n
+        return slot
+
+    def slot_vertices(self, slot: int) -> int:
+        return self._n[slot]
+
+    def _pinned_bytes(self, nbytes: int) -> np.ndarray:
+        import torch
+        return torch.empty(max(nbytes, 1), dtype=torch.uint8).pin_memory().numpy()
+
     def kernel_launches(self) -> int:
         return self.solver.kernel_launches()
 
@@ -83,7 +118,8 @@ class PoolBackend:
 
 
 class Request:
-    __slots__ = ("rp", "ci", "labels", "future", "t_submit", "t_admit", "t_done", "slot", "iterations")
+    __slots__ = ("rp", "ci", "labels", "future", "t_submit", "t_admit", "t_done", "slot", "iterations",
+                 "checkpoint", "blocked_steps", "resident_steps", "evictions")
 
     def __init__(self, rp, ci, host_buffer=None):
         self.rp = np.ascontiguousarray(rp, dtype=np.int32)
@@ -96,6 +132,10 @@ class Request:
         self.t_done = None
         self.slot = None
         self.iterations = None
+        self.checkpoint = None   # host checkpoint while evicted
+        self.blocked_steps = 0   # steps spent at the head of the queue without fitting
+        self.resident_steps = 0  # steps since (re-)admission
+        self.evictions = 0
 
 
 class Server:
@@ -103,9 +143,17 @@ class Server:
     resolving to ``(labels, iterations)``."""
 
     def __init__(self, hbm_budget_bytes: int = 1 << 30, max_slots: int = 256, iters_per_step: int = 1,
-                 backend=None, **opts):
+                 backend=None, preempt_after_steps: int = 0, max_evictions: int = 1, **opts):
         self.backend = backend if backend is not None else PoolBackend(hbm_budget_bytes, max_slots, **opts)
         self.iters_per_step = iters_per_step
+        # preemption under memory pressure (0 = off): when the request at the
+        # head of the queue has not fitted for this many steps, the resident
+        # graph that has run at least as many steps and holds the most memory
+        # is checkpointed to host memory (fastsv_pool_evict) and queued right
+        # behind the head; it resumes where it stopped (fastsv_pool_restore)
+        self.preempt_after_steps = preempt_after_steps
+        self.max_evictions = max_evictions
+        self.evictions = 0
         self._queue: collections.deque[Request] = collections.deque()
         self._resident: dict[int, Request] = {}
         self._cv = threading.Condition()
@@ -161,13 +209,39 @@ class Server:
     def _admit(self):
         while self._queue:
             req = self._queue[0]
-            slot = self.backend.add(req.rp, req.ci, req.labels)
+            if req.checkpoint is not None:
+                slot = self.backend.restore(req.rp, req.ci, req.labels, req.checkpoint)
+            else:
+                slot = self.backend.add(req.rp, req.ci, req.labels)
             if slot is None:
+                if self._preempt_for(req):
+                    continue  # memory was freed: try the head again
                 return  # full: keep arrival order, wait for a harvest
             self._queue.popleft()
             req.slot = slot
-            req.t_admit = time.perf_counter()
+            req.checkpoint = None
+            req.resident_steps = 0
+            req.blocked_steps = 0
+            if req.t_admit is None:
+                req.t_admit = time.perf_counter()
             self._resident[slot] = req
+
+    def _preempt_for(self, head: Request) -> bool:
+        k = self.preempt_after_steps
+        if k <= 0 or head.blocked_steps < k or head.evictions > 0:
+            return False  # off, not waiting long enough, or itself a preempted graph (no ping-pong)
+        victims = [r for r in self._resident.values()
+                   if r.resident_steps >= k and r.evictions < self.max_evictions]
+        if not victims:
+            return False
+        v = max(victims, key=lambda r: len(r.ci) + len(r.rp))
+        v.checkpoint = self.backend.evict(v.slot)
+        del self._resident[v.slot]
+        v.slot = None
+        v.evictions += 1
+        self.evictions += 1
+        self._queue.insert(1, v)  # resumes right after the request it made room for
+        return True
 
     def _run(self):
         try:
@@ -181,6 +255,11 @@ class Server:
                 if self._resident:
                     self.backend.step(self.iters_per_step)
                     self.steps += 1
+                    for r in self._resident.values():
+                        r.resident_steps += 1
+                    with self._cv:
+                        if self._queue:
+                            self._queue[0].blocked_steps += 1
                     done, _ = self.backend.poll()
                     now = time.perf_counter()
                     for slot, iters in done:

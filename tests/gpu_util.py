@@ -53,16 +53,40 @@ class Solver:
         self.s.close()
 
 
-def per_iteration_parity(rp, ci, bits=64, max_check=64, **kw):
+def ragged_graphs():
+    """Random graphs whose (rows + entries) land just below, on and above
+    multiples of the merge-path tile, plus hubs spanning many tiles."""
+    rng = np.random.default_rng(99)
+    out = []
+    for n, m_und in [(1, 0), (2, 1), (300, 200), (1000, 1500), (2047, 0), (2049, 1), (3000, 5000)]:
+        edges = {(int(rng.integers(n)), int(rng.integers(n))) for _ in range(m_und)}
+        edges = sorted({(min(u, v), max(u, v)) for u, v in edges if u != v})
+        out.append(oracle.csr_from_edges(n, edges))
+    # a hub adjacent to everything plus a sparse rest: one row spans many tiles
+    n = 9000
+    edges = [(0, i) for i in range(1, n, 2)] + [(i, i + 1) for i in range(1, n - 1, 7)]
+    out.append(oracle.csr_from_edges(n, edges))
+    out.append(graphgen.rmat(11, 8, seed=7, permute=True))
+    out.append(graphgen.grid(50, 0.55, 33, seed=5))
+    return out
+
+
+def per_iteration_parity(rp, ci, bits=64, max_check=64, variant=0, **kw):
     """Compare the device pointer graph with the oracle's after every
-    iteration (the device restarts with max_iters = k; the oracle steps)."""
+    iteration (the device restarts with max_iters = k; the oracle steps).
+    variant 1..4 selects the convergence ablation sv1..sv4."""
     import paper_1910_05971_gb300 as fsv
     n = len(rp) - 1
     f_ref = np.arange(n, dtype=np.int32)
+    if variant:
+        kw["variant"] = variant
     k = 0
     while True:
         k += 1
-        changed = oracle.iteration(rp, ci, f_ref)
+        if 1 <= variant <= 4:
+            changed = oracle.sv_iteration(rp, ci, f_ref, variant)
+        else:
+            changed = oracle.iteration(rp, ci, f_ref)
         got, st = gpu_solve(rp, ci, bits=bits, max_iters=k, **kw)
         assert np.array_equal(got, f_ref), f"pointer graph differs after iteration {k}"
         if changed == 0:

@@ -11,7 +11,7 @@ import pytest
 
 import graphgen
 import oracle
-from gpu_util import Solver, gpu_solve, oracle_batch, per_iteration_parity, to_dev, workload
+from gpu_util import Solver, gpu_solve, oracle_batch, per_iteration_parity, ragged_graphs, to_dev, workload
 
 pytestmark = pytest.mark.gpu
 
@@ -56,21 +56,7 @@ def test_exhaustive_small_graphs():
 
 
 def _ragged_graphs():
-    """Random graphs whose (rows + entries) land just below, on and above
-    multiples of the hooking tile, plus hubs spanning many tiles."""
-    rng = np.random.default_rng(99)
-    out = []
-    for n, m_und in [(1, 0), (2, 1), (300, 200), (1000, 1500), (2047, 0), (2049, 1), (3000, 5000)]:
-        edges = {(int(rng.integers(n)), int(rng.integers(n))) for _ in range(m_und)}
-        edges = sorted({(min(u, v), max(u, v)) for u, v in edges if u != v})
-        out.append(oracle.csr_from_edges(n, edges))
-    # a hub adjacent to everything plus a sparse rest: one row spans many tiles
-    n = 9000
-    edges = [(0, i) for i in range(1, n, 2)] + [(i, i + 1) for i in range(1, n - 1, 7)]
-    out.append(oracle.csr_from_edges(n, edges))
-    out.append(graphgen.rmat(11, 8, seed=7, permute=True))
-    out.append(graphgen.grid(50, 0.55, 33, seed=5))
-    return out
+    return ragged_graphs()
 
 
 @pytest.mark.parametrize("threads", [64, 256])

@@ -1,6 +1,6 @@
 """Pins for the oracle's convergence ablation sv1..sv5 (no GPU).
 
-sv1 is the simplified SV algorithm (Algorithm 1); sv2..sv5 add grandparent
+sv1 is the simplified SV algorithm (Algorithm 1, Section 2.4); sv2..sv5 add grandparent
 hooking (Section 3.1), stochastic hooking (3.2), aggressive hooking with
 Algorithm 2's single-pass body (3.3) and early termination (3.4) one at a
 time, so sv5 is Algorithm 2.  Each variant is checked against hand-worked

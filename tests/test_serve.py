@@ -122,3 +122,112 @@ def test_server_rejects_oversized_request():
         fut = srv.submit(rp, ci)
         with pytest.raises(ValueError):
             fut.result(timeout=10)
+
+
+def _oracle_after(rp, ci, k):
+    f = np.arange(len(rp) - 1, dtype=np.int32)
+    for _ in range(k):
+        oracle.iteration(rp, ci, f)
+    return f
+
+
+def _run_to_end(pool, slot_of, done, limit=10000):
+    steps = 0
+    while slot_of:
+        pool.step(1)
+        steps += 1
+        fin, _ = pool.poll()
+        for slot, iters in fin:
+            done[slot_of.pop(slot)] = iters
+        assert steps < limit
+
+
+def test_evict_and_restore_resume_exactly():
+    """A graph checkpointed after k iterations holds Algorithm 2's f and
+    f[f] after k iterations; restored later (into the same pool while others
+    run, or into another pool) it finishes with the labels and iteration count
+    of an uninterrupted solve."""
+    import paper_1910_05971_gb300 as fsv
+    from paper_1910_05971_gb300.serve import PoolBackend
+    graphs = [graphgen.grid(80, 0.55, 0, seed=11), graphgen.grid(60, 0.6, 7, seed=12),
+              graphgen.rmat(12, 16, seed=13), oracle.csr_from_edges(3000, [(j, j + 1) for j in range(2999)])]
+    graphs = [(rp.astype(np.int32), ci.astype(np.int32)) for rp, ci in graphs]
+    ref = _alone(graphs)
+    assert all(it > 3 for _, it in ref)  # all still iterating after two steps
+    pool = PoolBackend(64 << 20, 8)
+    other = PoolBackend(64 << 20, 8)
+    labels = [np.full(len(rp) - 1, -1, np.int32) for rp, _ in graphs]
+    slot_of = {}
+    for g, (rp, ci) in enumerate(graphs):
+        slot_of[pool.add(rp, ci, labels[g])] = g
+    pool.step(1)
+    pool.step(1)
+    assert pool.poll()[0] == []
+    _, _, bytes_before = fsv.fastsv_pool_usage(pool.h)
+    evicted = {}
+    for slot, g in list(slot_of.items()):
+        if g in (0, 3):
+            ck = pool.evict(slot)
+            del slot_of[slot]
+            evicted[g] = ck
+            rp, ci = graphs[g]
+            n = len(rp) - 1
+            f = ck[64:64 + 4 * n].view(np.int32)
+            gf = ck[64 + 4 * n:64 + 8 * n].view(np.int32)
+            assert np.array_equal(f, _oracle_after(rp, ci, 2))
+            assert np.array_equal(gf, f[f])
+    _, used, bytes_after = fsv.fastsv_pool_usage(pool.h)
+    assert used == 2
+    assert bytes_before - bytes_after == sum(fsv.fastsv_pool_bytes(len(graphs[g][0]) - 1, len(graphs[g][1]))
+                                             for g in evicted)
+    pool.step(1)  # the others go on without them
+    # graph 0 comes back into the same pool, graph 3 into another one
+    rp, ci = graphs[0]
+    slot_of[pool.restore(rp, ci, labels[0], evicted[0])] = 0
+    other_slots = {}
+    rp, ci = graphs[3]
+    other_slots[other.restore(rp, ci, labels[3], evicted[3])] = 3
+    done = {}
+    _run_to_end(pool, slot_of, done)
+    _run_to_end(other, other_slots, done)
+    for g, (f, it) in enumerate(ref):
+        assert np.array_equal(labels[g], f), g
+        assert done[g] == it, (g, done[g], it)
+    pool.close()
+    other.close()
+
+
+def test_evict_and_restore_errors():
+    import paper_1910_05971_gb300 as fsv
+    from paper_1910_05971_gb300.serve import PoolBackend
+    rp, ci = graphgen.grid(40, 0.6, 0, seed=21)
+    rp, ci = rp.astype(np.int32), ci.astype(np.int32)
+    small = oracle.csr_from_edges(2, [(0, 1)])
+    small = (small[0].astype(np.int32), small[1].astype(np.int32))
+    pool = PoolBackend(16 << 20, 4)
+    lab = np.empty(len(rp) - 1, np.int32)
+    buf = np.zeros(fsv.fastsv_pool_checkpoint_bytes(len(rp) - 1), np.uint8)
+    assert fsv.fastsv_pool_evict(pool.h, 0, buf.ctypes.data) == fsv.FASTSV_ERR_INVALID_ARG  # free slot
+    s = pool.add(rp, ci, lab)
+    # added but not stepped yet: nothing to checkpoint
+    assert fsv.fastsv_pool_evict(pool.h, s, buf.ctypes.data) == fsv.FASTSV_ERR_INVALID_ARG
+    lab2 = np.empty(2, np.int32)
+    s2 = pool.add(small[0], small[1], lab2)
+    pool.step(2)  # the 2-vertex graph finishes in 2 iterations; the lattice does not
+    assert fsv.fastsv_pool_evict(pool.h, s2, buf.ctypes.data) == fsv.FASTSV_ERR_INVALID_ARG  # finished
+    ck = pool.evict(s)
+    bad = ck.copy()
+    bad[0] ^= 0xFF
+    assert fsv.fastsv_pool_restore(pool.h, len(rp) - 1, rp.ctypes.data, ci.ctypes.data, lab.ctypes.data,
+                                   bad.ctypes.data)[0] == fsv.FASTSV_ERR_INVALID_ARG
+    # a checkpoint of another graph (n differs)
+    assert fsv.fastsv_pool_restore(pool.h, 2, small[0].ctypes.data, small[1].ctypes.data, lab2.ctypes.data,
+                                   ck.ctypes.data)[0] == fsv.FASTSV_ERR_INVALID_ARG
+    fin, _ = pool.poll()
+    assert [x[0] for x in fin] == [s2]
+    slot = pool.restore(rp, ci, lab, ck)
+    done = {}
+    _run_to_end(pool, {slot: 0}, done)
+    f, it, _, _ = oracle.fastsv(rp, ci)
+    assert np.array_equal(lab, f) and done[0] == it
+    pool.close()

@@ -4,6 +4,7 @@ Checks admission order, back-pressure when the pool is full, rejection of
 requests larger than the budget, equality with solving alone, and that a
 failing backend fails every outstanding request instead of hanging."""
 import threading
+import time
 
 import numpy as np
 import pytest
@@ -12,7 +13,7 @@ import oracle
 
 
 class FakePool:
-    def __init__(self, budget, max_slots, fail_after_steps=None):
+    def __init__(self, budget, max_slots, fail_after_steps=None, step_delay=0.0):
         self.budget = budget
         self.max_slots = max_slots
         self.used = 0
@@ -21,6 +22,8 @@ class FakePool:
         self.max_resident = 0
         self.steps = 0
         self.fail_after_steps = fail_after_steps
+        self.step_delay = step_delay
+        self.evicted = 0
 
     def bytes_for(self, n, m):
         return 4 * (n + 1) + 4 * max(m, 1) + 12 * n
@@ -39,6 +42,8 @@ class FakePool:
         return slot
 
     def step(self, iters):
+        if self.step_delay:
+            time.sleep(self.step_delay)
         self.steps += 1
         if self.fail_after_steps is not None and self.steps > self.fail_after_steps:
             raise RuntimeError("device lost (simulated)")
@@ -50,6 +55,20 @@ class FakePool:
                 s["iters"] += 1
                 if ch == 0:
                     s["done"] = True
+
+    def evict(self, slot):
+        s = self.slots.pop(slot)
+        assert not s["done"] and s["iters"] > 0
+        self.used -= s["bytes"]
+        self.evicted += 1
+        return dict(f=s["f"].copy(), iters=s["iters"])
+
+    def restore(self, rp, ci, labels, ck):
+        slot = self.add(rp, ci, labels)
+        if slot is not None:
+            self.slots[slot]["f"] = ck["f"].copy()
+            self.slots[slot]["iters"] = ck["iters"]
+        return slot
 
     def poll(self):
         out = []
@@ -138,3 +157,44 @@ def test_concurrent_submitters():
     for i, (rp, ci) in enumerate(graphs):
         f, it, _, _ = oracle.fastsv(rp, ci)
         assert np.array_equal(results[i][0], f) and results[i][1] == it
+
+
+def test_preemption_lets_small_requests_pass_and_resumes_exactly():
+    """A long-running graph fills the pool; with preemption on, requests that
+    cannot fit make the server checkpoint it, run one of them, and resume it:
+    every result equals solving alone, and a small request no longer waits for
+    the long graph to finish."""
+    from paper_1910_05971_gb300.serve import Server
+    n = 400
+    long_path = oracle.csr_from_edges(n, [(i, i + 1) for i in range(n - 1)])  # ~log-many iterations, big
+    smalls = _graphs(6, seed=5)
+    pool_bytes = FakePool(0, 1).bytes_for(n, len(long_path[1]))
+
+    def run(preempt):
+        backend = FakePool(pool_bytes + 64, 8, step_delay=0.01)
+        srv = Server(backend=backend, preempt_after_steps=preempt)
+        futs = [srv.submit(*long_path)]
+        # let the long graph start (it needs 9 steps), then queue the small ones
+        t0 = time.time()
+        while backend.steps < 1 and time.time() - t0 < 30:
+            time.sleep(0.0005)
+        futs += [srv.submit(rp, ci) for rp, ci in smalls]
+        res = [f.result(timeout=60) for f in futs]
+        srv.close()
+        return res, backend, srv
+
+    def is_long(r):
+        return len(r.rp) == n + 1
+
+    for preempt in (0, 2):
+        res, backend, srv = run(preempt)
+        for (rp, ci), (lab, it) in zip([long_path] + smalls, res):
+            f, it_ref, _, _ = oracle.fastsv(rp, ci)
+            assert np.array_equal(lab, f) and it == it_ref
+        if preempt:
+            assert backend.evicted >= 1 and srv.evictions == backend.evicted
+            # a small request finished before the long graph instead of waiting for it
+            assert not is_long(srv.completed[0])
+        else:
+            assert backend.evicted == 0
+            assert is_long(srv.completed[0])
