@@ -88,6 +88,13 @@ __global__ void k_pool_admit(Ctx* ctx, Seg* segs, int32_t* k2_seg, int32_t* k2_r
     }
 }
 
+// start of a step: the device loop's iteration counter and cap
+__global__ void k_pool_begin(Ctx* ctx, int32_t loop_limit) {
+    ctx->loop_iter = 0;
+    ctx->loop_limit = loop_limit;
+    ctx->k3_done = 0;
+}
+
 struct Slot {
     int state = 0;  // 0 free, 1 admitted (copies in flight), 2 iterating on the device
     int64_t n = 0, m = 0;
@@ -439,6 +446,10 @@ fastsv_status fastsv_pool_step(fastsv_t h, int32_t iters, void* stream) {
     if (any) {
         h->loop_limit_host = iters;
         const bool graph = h->opt.use_graph != 0;
+        // every step runs up to `iters` iterations, whether or not it admitted
+        k_pool_begin<<<1, 1, 0, s>>>(P->d_ctx, iters);
+        h->launches += 1;
+        FSV_CUDA(h, cudaGetLastError());
         fastsv_status st = run_loop(h, P->d_ctx, 0, 0, items, 0, s);
         if (st != FASTSV_OK) return st;
         if (graph) {
@@ -498,6 +509,7 @@ fastsv_status fastsv_pool_poll(fastsv_t h, int32_t* done_slots, int32_t* done_it
             arena_free(P, S.off, S.bytes);
             S = Slot();
         }
+        P->dirty = true;  // the next step's tile lists leave the finished graphs out
     }
     *n_done = nd;
     if (n_active) *n_active = act;

@@ -113,15 +113,19 @@ __global__ void __launch_bounds__(256) k_close(Ctx* ctx, cudaGraphConditionalHan
 // asynchronous mode: one fused kernel per iteration on the single vector f
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ int32_t ld_live(const int32_t* p) { return __ldcg(p); }
+// loads of the parent vector that other threads lower while the kernel runs:
+// plain loads (L1 may serve an older value, which can only delay a hook; an
+// iteration in which nothing is lowered reads the final values everywhere)
+__device__ __forceinline__ int32_t ld_live(const int32_t* p) { return *p; }
 
 // Merge-path tiles as in k2_spmv (phases 1 and 2 are the same walk over row
 // ends and entries); the values gathered are the live parents f[v], and
-// phase 3 hooks and shortcuts at once.  The counter receives, per tile, the
+// phase 3 hooks and shortcuts at once.  f is deliberately not __restrict__:
+// it is read and lowered by atomics in the same kernel.  The counter receives, per tile, the
 // number of rows whose processing lowered some entry of f (at most one per
 // row and tile, so it cannot wrap).
 template <typename RP, int THREADS, int ITEMS>
-__global__ void __launch_bounds__(THREADS) k_async(Ctx* __restrict__ ctx) {
+__global__ void __launch_bounds__(THREADS, 5) k_async(Ctx* __restrict__ ctx) {
     constexpr int TILE = THREADS * ITEMS;
     extern __shared__ int32_t smem[];
     int32_t* s_rowend = smem;                // row ends (tile-relative)
@@ -200,20 +204,31 @@ __global__ void __launch_bounds__(THREADS) k_async(Ctx* __restrict__ ctx) {
         }
         if (acc != INF && r >= 0 && r < R) atomicMin(&s_min[r], acc);
         __syncthreads();
-        // phase 3: hook onto the row minimum, then shortcut the row's vertex
+        // phase 3, per row u with row minimum mn: with fu = f[u] and
+        // g = f[fu] (loaded for all of a thread's rows first, independent
+        // loads), hook the parent f[fu] <-min mn (stochastic; a no-op unless
+        // mn < g) and set f[u] <-min min(mn, g) (aggressive hook and
+        // shortcut in one).  An iteration without any lowering therefore
+        // saw mn >= f[u] on every row and f[f[u]] == f[u] everywhere.
+        constexpr int RPT = ITEMS + 1;  // rows per thread: R <= TILE + 1
+        int32_t mn[RPT], fu[RPT], g[RPT];
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) {
+            const int i = tid + q * THREADS;
+            mn[q] = i < R ? s_min[i] : INF;
+            fu[q] = i < R ? ld_live(f + x0 + i) : 0;
+        }
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) g[q] = tid + q * THREADS < R ? ld_live(f + fu[q]) : 0;
         unsigned cnt = 0;
-        for (int i = tid; i < R; i += THREADS) {
-            const int64_t u = x0 + i;
-            const int32_t mn = s_min[i];
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) {
+            const int i = tid + q * THREADS;
+            if (i >= R) continue;
             bool low = false;
-            int32_t fu = ld_live(f + u);
-            if (mn < fu) {
-                low |= atomicMin(f + fu, mn) > mn;  // hook the parent (stochastic)
-                low |= atomicMin(f + u, mn) > mn;   // hook the vertex (aggressive)
-                fu = mn < fu ? mn : fu;
-            }
-            const int32_t g = ld_live(f + fu);       // shortcut f[u] <-min f[f[u]]
-            if (g < fu) low |= atomicMin(f + u, g) > g;
+            if (mn[q] < g[q]) low |= atomicMin(f + fu[q], mn[q]) > mn[q];
+            const int32_t t = mn[q] < g[q] ? mn[q] : g[q];
+            if (t < fu[q]) low |= atomicMin(f + x0 + i, t) > t;
             cnt += low;
         }
         cnt = __reduce_add_sync(0xffffffffu, cnt);

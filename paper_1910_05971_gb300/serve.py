@@ -53,8 +53,8 @@ class PoolBackend:
 
     def host_buffer(self, n: int) -> np.ndarray:
         """int32 host buffer for a graph's labels, in pinned memory so that the
-        device-to-host copy of a harvest runs at full link speed (torch's
-        pinned-memory cache makes reuse cheap)."""
+        device-to-host copy of a harvest runs at full link speed.  Pinning is
+        slow: allocate these ahead of time and reuse them."""
         import torch
         return torch.empty(max(n, 1), dtype=torch.int32).pin_memory().numpy()
 
@@ -121,11 +121,14 @@ class Request:
     __slots__ = ("rp", "ci", "labels", "future", "t_submit", "t_admit", "t_done", "slot", "iterations",
                  "checkpoint", "blocked_steps", "resident_steps", "evictions")
 
-    def __init__(self, rp, ci, host_buffer=None):
+    def __init__(self, rp, ci, labels=None):
         self.rp = np.ascontiguousarray(rp, dtype=np.int32)
         self.ci = np.ascontiguousarray(ci, dtype=np.int32)
         n = max(len(self.rp) - 1, 1)
-        self.labels = host_buffer(n) if host_buffer is not None else np.empty(n, dtype=np.int32)
+        if labels is None:
+            labels = np.empty(n, dtype=np.int32)
+        assert labels.dtype == np.int32 and labels.flags.c_contiguous and len(labels) >= len(self.rp) - 1
+        self.labels = labels
         self.future: Future = Future()
         self.t_submit = time.perf_counter()
         self.t_admit = None
@@ -165,8 +168,13 @@ class Server:
         self._thread.start()
 
     # -- client side ------------------------------------------------------
-    def submit(self, rp, ci) -> Future:
-        req = Request(rp, ci, getattr(self.backend, "host_buffer", None))
+    def submit(self, rp, ci, labels=None) -> Future:
+        """Queue one graph (int32 CSR in host memory).  ``labels``: optional
+        int32 host buffer of n entries that receives the result; a pinned one
+        (e.g. from ``PoolBackend.host_buffer``, allocated ahead of time)
+        makes the copy back asynchronous.  Pinning host memory is slow, so it
+        is not done per request."""
+        req = Request(rp, ci, labels)
         n = len(req.rp) - 1
         if self.backend.bytes_for(n, len(req.ci)) > self.backend.budget:
             req.future.set_exception(ValueError("graph larger than the pool's HBM budget"))

@@ -150,7 +150,7 @@ def test_evict_and_restore_resume_exactly():
     import paper_1910_05971_gb300 as fsv
     from paper_1910_05971_gb300.serve import PoolBackend
     graphs = [graphgen.grid(80, 0.55, 0, seed=11), graphgen.grid(60, 0.6, 7, seed=12),
-              graphgen.rmat(12, 16, seed=13), oracle.csr_from_edges(3000, [(j, j + 1) for j in range(2999)])]
+              graphgen.rmat(12, 4, seed=13), oracle.csr_from_edges(3000, [(j, j + 1) for j in range(2999)])]
     graphs = [(rp.astype(np.int32), ci.astype(np.int32)) for rp, ci in graphs]
     ref = _alone(graphs)
     assert all(it > 3 for _, it in ref)  # all still iterating after two steps
