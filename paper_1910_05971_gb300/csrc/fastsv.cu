@@ -558,39 +558,46 @@ static fastsv_status launch_block_build(fastsv_ctx* h, int nb, int shift, int64_
     const int64_t np1 = n + 1;
     const int64_t chunks = (np1 + SCAN_CHUNK - 1) / SCAN_CHUNK;
     const int smem_count = block_build_smem(nb);
-    const int smem_sorted = block_scatter_smem(nb);
     const void* fc = (const void*)k_block_count<RP>;
-    const void* fs = (const void*)k_block_scatter_sorted<RP>;
     const void* fr = (const void*)k_block_scatter<RP>;
     FSV_CUDA(h, cudaFuncSetAttribute(fc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_count));
-    FSV_CUDA(h, cudaFuncSetAttribute(fs, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_sorted));
     FSV_CUDA(h, cudaFuncSetAttribute(fr, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_count));
     Ctx* ctx = h->d_ctx;
     int32_t* flag = h->d_sums + h->cap_sums - 1;  // "some row is not sorted by column"
-    FSV_CUDA(h, cudaMemsetAsync(h->d_counts, 0, (size_t)nb * np1 * 4, s));
+    int32_t* start = h->d_rpB;                    // run starts first, then the block row pointers
     FSV_CUDA(h, cudaMemsetAsync(flag, 0, sizeof(int32_t), s));
+    // sorted rows: run starts, counts as their differences
+    k_block_starts<RP><<<g, BS_THREADS, 0, s>>>(ctx, start, nb, shift, flag);
+    k_block_counts<RP><<<g, 256, 0, s>>>(ctx, start, h->d_counts, nb, flag);
     {
+        // unsorted rows: count per (row, block) instead (returns at once otherwise)
         void* a[] = {(void*)&ctx, (void*)&h->d_counts, (void*)&nb, (void*)&shift, (void*)&flag};
         FSV_CUDA(h, cudaLaunchKernel(fc, dim3(g), dim3(BUILD_THREADS), a, (size_t)smem_count, s));
     }
+    // block row pointers: exclusive scan of every block's counts
     int ch = (int)chunks;
     k_scan_chunk_sums<<<(unsigned)(nb * chunks), SCAN_THREADS, 0, s>>>(h->d_counts, np1, ch, h->d_sums);
     k_scan_sums<<<nb, 1024, 0, s>>>(h->d_sums, ch);
-    k_scan_apply<<<(unsigned)(nb * chunks), SCAN_THREADS, 0, s>>>(h->d_counts, h->d_rpB, np1, ch, h->d_sums);
+    // the starts are read by the run scatter: the row pointers go to the
+    // counts buffer, which the scan no longer needs once applied in place
+    k_scan_apply<<<(unsigned)(nb * chunks), SCAN_THREADS, 0, s>>>(h->d_counts, h->d_counts, np1, ch, h->d_sums);
     {
-        // sorted rows: every entry's destination in closed form
-        void* a[] = {(void*)&ctx, (void*)&h->d_rpB, (void*)&h->d_counts, (void*)&h->d_colB, (void*)&nb,
+        const void* fs = (const void*)k_block_scatter_runs<RP>;
+        const int smem_runs = runs_smem(nb);
+        FSV_CUDA(h, cudaFuncSetAttribute(fs, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_runs));
+        void* a[] = {(void*)&ctx, (void*)&h->d_counts, (void*)&start, (void*)&h->d_colB, (void*)&nb,
                      (void*)&shift, (void*)&flag};
-        FSV_CUDA(h, cudaLaunchKernel(fs, dim3(g), dim3(BUILD_THREADS), a, (size_t)smem_sorted, s));
+        FSV_CUDA(h, cudaLaunchKernel(fs, dim3(g), dim3(BS_THREADS), a, (size_t)smem_runs, s));
     }
     {
-        // otherwise: ranks from atomics, counts reused as per-(row, block) cursors
-        FSV_CUDA(h, cudaMemsetAsync(h->d_counts, 0, (size_t)nb * np1 * 4, s));
-        void* a[] = {(void*)&ctx, (void*)&h->d_rpB, (void*)&h->d_counts, (void*)&h->d_colB, (void*)&nb,
+        // unsorted rows: ranks from atomics; the run-start buffer becomes the
+        // per-(row, block) cursors
+        k_zero_if_unsorted<<<g, 256, 0, s>>>(start, (int64_t)nb * np1, flag);
+        void* a[] = {(void*)&ctx, (void*)&h->d_counts, (void*)&start, (void*)&h->d_colB, (void*)&nb,
                      (void*)&shift, (void*)&flag};
         FSV_CUDA(h, cudaLaunchKernel(fr, dim3(g), dim3(BUILD_THREADS), a, (size_t)smem_count, s));
     }
-    h->pending_fixed_launches += 6;
+    h->pending_fixed_launches += 9;
     FSV_CUDA(h, cudaGetLastError());
     return FASTSV_OK;
 }
@@ -682,7 +689,7 @@ static fastsv_status solve_single(fastsv_ctx* h, int64_t n, int64_t m, const voi
         st = rp64 ? launch_block_build<int64_t>(h, nb_eff, shift, n, s)
                   : launch_block_build<int32_t>(h, nb_eff, shift, n, s);
         if (st != FASTSV_OK) return st;
-        k_setup_blocks<<<1, 1, 0, s>>>(h->d_ctx, h->d_rpB, h->d_colB, nb_eff, (int32_t)tile);
+        k_setup_blocks<<<1, 1, 0, s>>>(h->d_ctx, h->d_counts, h->d_colB, nb_eff, (int32_t)tile);
         k_scan_tiles<<<1, 1024, 0, s>>>(h->d_ctx);
         k_partition<int32_t><<<setup_grid(h), 256, 0, s>>>(h->d_ctx);
         h->pending_fixed_launches += 3;

@@ -420,7 +420,7 @@ __device__ __forceinline__ void tile_walk(const int32_t* s_rowend, int nfull, in
 
 // per tile of the graph's own merge-path partition (segment 0): row ends,
 // column ids, row count R, entry count E; returns false for an empty tile
-template <typename RP>
+template <typename RP, int ITEMS = BUILD_ITEMS>
 __device__ __forceinline__ bool load_tile(const Seg& S, int64_t t, int64_t tile, const int32_t* tile_row,
                                           int32_t* s_rowend, int32_t* s_col, int64_t& x0, int& nfull, int& R,
                                           int& E, int& D) {
@@ -436,8 +436,7 @@ __device__ __forceinline__ bool load_tile(const Seg& S, int64_t t, int64_t tile,
     R = nfull + (x1 < n ? 1 : 0);
     E = (int)(y1 - y0);
     D = (int)(d1 - d0);
-    // loads first, stores after (clamped addresses), ITEMS = tile / blockDim
-    constexpr int ITEMS = BUILD_ITEMS;  // upper bound; the loops stop at the tile size
+    // loads first, stores after (clamped addresses); ITEMS bounds tile / blockDim
     const int per = (int)(tile / blockDim.x);
     int64_t e[ITEMS + 1];
     int32_t c[ITEMS];
@@ -479,18 +478,18 @@ __device__ __forceinline__ int row_start_local(const int32_t* s_rowend, int r) {
     return r > 0 ? s_rowend[r - 1] : 0;
 }
 
-// counts[b][u] = entries of row u whose column lies in block b.  Every
-// thread counts its ITEMS merge-path items in one register (4 bits per
-// block), so shared-memory atomics happen once per (thread, row, block), not
-// per entry.  Rows that start and end inside the tile are stored, the two
-// that can continue in a neighbouring tile are added atomically.  The kernel
-// also records whether any row is not sorted by column (then the scatter
-// falls back to ranking entries with atomics).
+// Rows not sorted by column: counts[b][u] = entries of row u whose column
+// lies in block b.  Every thread counts its ITEMS merge-path items in one
+// register (4 bits per block), so shared-memory atomics happen once per
+// (thread, row, block), not per entry.  Rows that start and end inside the
+// tile are stored, the two that can continue in a neighbouring tile are
+// added atomically.  Returns at once for sorted graphs.
 template <typename RP>
 __global__ void __launch_bounds__(BUILD_THREADS)
     k_block_count(Ctx* ctx, int32_t* counts, int nb, int shift, int32_t* unsorted) {
     constexpr int TILE = BUILD_TILE;
     constexpr int RS = TILE + 1;
+    if (!*unsorted) return;  // sorted rows: counted from k_block_starts
     extern __shared__ int32_t smem[];
     int32_t* s_rowend = smem;
     int32_t* s_col = smem + RS;
@@ -561,6 +560,177 @@ __global__ void __launch_bounds__(BUILD_THREADS)
         __syncthreads();
     }
     if (bad) atomicOr(unsorted, 1);
+}
+
+// ---------------------------------------------------------------------------
+// column-block build for rows sorted by column (the common case): one
+// streaming pass finds where each (row, block) run starts, counts are the
+// differences of those starts, and the scatter copies each run in order
+// ---------------------------------------------------------------------------
+
+constexpr int BS_THREADS = 256;  // 256 threads x 4 items: the build tiles (BUILD_TILE items)
+constexpr int BS_ITEMS = BUILD_TILE / BS_THREADS;
+
+// tile row of every entry of the tile: each thread walks its BS_ITEMS
+// merge-path items (shared memory only), so the passes after it can take the
+// entries in striped order, where consecutive threads touch consecutive
+// entries and their global accesses coalesce
+__device__ __forceinline__ void tile_rows_of_entries(const int32_t* s_rowend, int32_t* s_rowof, int nfull, int D) {
+    const int k0 = threadIdx.x * BS_ITEMS;
+    if (k0 >= D) return;
+    int lo = 0, hi = nfull;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (s_rowend[mid] + mid < k0)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    int r = lo, y = k0 - lo;
+    int rend = r < nfull ? s_rowend[r] : 0x7fffffff;
+    const int steps = min(BS_ITEMS, D - k0);
+    for (int k = 0; k < steps; ++k) {
+        if (y >= rend) {
+            ++r;
+            rend = r < nfull ? s_rowend[r] : 0x7fffffff;
+        } else {
+            s_rowof[y++] = r;
+        }
+    }
+}
+
+// start[k][u] = position of the first entry of row u whose column block is
+// >= k, or the row end if there is none (k-major, stride n+1).  For a row
+// sorted by column, block k's run of row u is [start[k][u], start[k+1][u])
+// (the row end for the last block).  Every (k, u) is written exactly once:
+// by the entry that opens a run (for the blocks after the previous entry's
+// block, up to its own) or at the row end (for the blocks after the row's
+// last entry).  An entry whose block is below its predecessor's marks the
+// graph as unsorted, and the build then takes the ranked path instead.
+template <typename RP>
+__global__ void __launch_bounds__(BS_THREADS, 5)
+    k_block_starts(Ctx* ctx, int32_t* start, int nb, int shift, int32_t* unsorted) {
+    __shared__ int32_t s_rowend[BUILD_TILE + 1];
+    __shared__ int32_t s_col[BUILD_TILE];
+    __shared__ int32_t s_rowof[BUILD_TILE];
+    const Seg& S = ctx->segs[0];
+    const RP* rp = (const RP*)S.rp;
+    const int32_t* ci = S.ci;
+    const int64_t np1 = S.n + 1;
+    const int64_t T = S.k2_ntiles;
+    int bad = 0;
+    for (int64_t t = blockIdx.x; t < T; t += gridDim.x) {
+        int64_t x0;
+        int nfull, R, E, D;
+        if (!load_tile<RP, BS_ITEMS>(S, t, BUILD_TILE, ctx->k2_tile_row, s_rowend, s_col, x0, nfull, R, E, D))
+            continue;
+        const int64_t y0 = t * (int64_t)BUILD_TILE - x0;
+        const bool first_whole = rp_at(rp, x0) >= y0;
+        // block of the last entry of row 0 before this tile (the row began earlier)
+        const int carry = (!first_whole && y0 > 0) ? col_block(ci[y0 - 1], shift, nb) : -1;
+        __syncthreads();
+        tile_rows_of_entries(s_rowend, s_rowof, nfull, D);
+        __syncthreads();
+        // entries that open a block run of their row
+        for (int y = threadIdx.x; y < E; y += BS_THREADS) {
+            const int r = s_rowof[y];
+            const int b = col_block(s_col[y], shift, nb);
+            const int pb = y > row_start_local(s_rowend, r) ? col_block(s_col[y - 1], shift, nb) : (r == 0 ? carry : -1);
+            if (b < pb) {
+                bad = 1;
+                continue;
+            }
+            for (int kk = pb + 1; kk <= b; ++kk) start[kk * np1 + x0 + r] = (int32_t)(y0 + y);
+        }
+        // row ends: the blocks after each row's last entry
+        for (int r = threadIdx.x; r < nfull; r += BS_THREADS) {
+            const int rs = row_start_local(s_rowend, r), re = s_rowend[r];
+            const int lastb = re > rs ? col_block(s_col[re - 1], shift, nb) : (r == 0 ? carry : -1);
+            for (int kk = lastb + 1; kk < nb; ++kk) start[kk * np1 + x0 + r] = (int32_t)(y0 + re);
+        }
+        __syncthreads();
+    }
+    if (bad) atomicOr(unsorted, 1);
+}
+
+// counts[k][u] = start[k+1][u] - start[k][u] (row end for the last block),
+// counts[k][n] = 0; all zero when the graph is unsorted (the ranked path's
+// counting kernel then fills them)
+template <typename RP>
+__global__ void k_block_counts(const Ctx* ctx, const int32_t* start, int32_t* counts, int nb, const int32_t* unsorted) {
+    const Seg& S = ctx->segs[0];
+    const RP* rp = (const RP*)S.rp;
+    const int64_t n = S.n, np1 = n + 1;
+    const bool zero = *unsorted != 0;
+    const int64_t total = (int64_t)nb * np1;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(i / np1);
+        const int64_t u = i - (int64_t)k * np1;
+        int32_t c = 0;
+        if (!zero && u < n) {
+            const int64_t next = k + 1 < nb ? (int64_t)start[i + np1] : rp_at(rp, u + 1);
+            c = (int32_t)(next - start[i]);
+        }
+        counts[i] = c;
+    }
+}
+
+__global__ void k_zero_if_unsorted(int32_t* p, int64_t count, const int32_t* unsorted) {
+    if (!*unsorted) return;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = 0;
+}
+
+// sorted rows: entry e of row u in block b goes to
+//   base_b + rpB[b][u] + (e - start[b][u]);
+// the per-(row, block) offsets of a tile are loaded once into shared memory,
+// then the entries are copied in striped order (coalesced stores)
+constexpr int runs_smem(int nb) { return nb * (BUILD_TILE + 1) * (int)sizeof(int32_t); }
+
+template <typename RP>
+__global__ void __launch_bounds__(BS_THREADS, 4)
+    k_block_scatter_runs(Ctx* ctx, const int32_t* rpB, const int32_t* start, int32_t* colB, int nb, int shift,
+                         const int32_t* unsorted) {
+    if (*unsorted) return;
+    constexpr int RS = BUILD_TILE + 1;
+    __shared__ int32_t s_rowend[BUILD_TILE + 1];
+    __shared__ int32_t s_col[BUILD_TILE];
+    __shared__ int32_t s_rowof[BUILD_TILE];
+    __shared__ long long s_blockbase[MAX_COL_BLOCKS];
+    extern __shared__ int32_t s_off[];  // [nb][RS]: rpB[b][u] - start[b][u]
+    const Seg& S = ctx->segs[0];
+    const int64_t np1 = S.n + 1;
+    const int64_t m = S.m;
+    const int64_t T = S.k2_ntiles;
+    if (threadIdx.x == 0) {
+        long long acc = 0;
+        for (int b = 0; b < nb; ++b) {
+            s_blockbase[b] = acc;
+            acc += rpB[(int64_t)b * np1 + S.n];
+        }
+    }
+    for (int64_t t = blockIdx.x; t < T; t += gridDim.x) {
+        int64_t x0;
+        int nfull, R, E, D;
+        if (!load_tile<RP, BS_ITEMS>(S, t, BUILD_TILE, ctx->k2_tile_row, s_rowend, s_col, x0, nfull, R, E, D))
+            continue;
+        const int64_t y0 = t * (int64_t)BUILD_TILE - x0;
+        for (int i = threadIdx.x; i < nb * R; i += BS_THREADS) {
+            const int b = i / R, r = i - b * R;
+            const int64_t g = (int64_t)b * np1 + x0 + r;
+            s_off[b * RS + r] = rpB[g] - start[g];
+        }
+        __syncthreads();
+        tile_rows_of_entries(s_rowend, s_rowof, nfull, D);
+        __syncthreads();
+        for (int y = threadIdx.x; y < E; y += BS_THREADS) {
+            const int32_t c = s_col[y];
+            const int b = col_block(c, shift, nb);
+            const long long pos = s_blockbase[b] + s_off[b * RS + s_rowof[y]] + y0 + y;
+            if (pos >= 0 && pos < m) colB[pos] = c;
+        }
+        __syncthreads();
+    }
 }
 
 // With every row sorted by column, the entries of row u that fall in block
@@ -964,7 +1134,7 @@ __global__ void __launch_bounds__(THREADS) k2_spmv(Ctx* __restrict__ ctx, int bl
             if (whole) {
                 if (!merge)
                     mngf[x0 + i] = mn;
-                else if (mn < mngf[x0 + i])
+                else if (mn != INF && mn < mngf[x0 + i])  // a row without entries in this block reads nothing
                     mngf[x0 + i] = mn;
             } else if (mn != INF) {
                 atomicMin(mngf + x0 + i, mn);
