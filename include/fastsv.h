@@ -89,9 +89,12 @@ typedef struct {
     int32_t timing;        /* 1: record device time of each call with CUDA events (default 1) */
     int32_t fail_alloc_after; /* test hook: >0 makes the N-th workspace allocation of this handle fail
                                  (returns FASTSV_ERR_OOM); 0 off */
-    int32_t col_blocks;    /* column blocks of the SpMV for one large graph: 0 = automatic (currently: none)
-                              1 = never, 2..16 = that many (each call then copies the CSR once into
-                              column-block order; worth it only for graphs needing many iterations) */
+    int32_t col_blocks;    /* column blocks of the SpMV for one large graph: 0 = automatic (blocks when
+                              4n bytes >= 1.5x the L2 and m >= 8n, one block per 64 MiB of the
+                              gathered vector), 1 = never, 2..16 = that many.  A blocked call copies
+                              col_idx once into column-block order (needs m <= 2^31 - 1 and 4m + 8nb(n+1)
+                              bytes of workspace) and runs one SpMV launch per block, whose gathers
+                              then hit an L2-resident slice of the grandparent vector */
     int32_t k2_threads;    /* threads per CTA of the SpMV kernel: 256 (default) or 64 */
     int32_t sparse_div;    /* single-graph calls: an iteration pushes from the vertices whose grandparent
                               changed (SpMSpV, Section 4.2) instead of a full SpMV when the degree sum of
@@ -237,6 +240,12 @@ fastsv_status fastsv_pool_step(fastsv_t h, int32_t iters, void* stream);
  */
 fastsv_status fastsv_pool_poll(fastsv_t h, int32_t* done_slots, int32_t* done_iters, int32_t cap, int32_t* n_done,
                                int32_t* n_active);
+
+/* Device time of the last step's phases (timing = 1): ms_out[0] waiting for
+ * the copies of graphs admitted since the step before, ms_out[1] admitting
+ * them and rebuilding the tile lists, ms_out[2] the iterations.  Waits for
+ * the step; all zero when timing is off. */
+fastsv_status fastsv_pool_step_times(fastsv_t h, float* ms_out);
 
 /* Pool occupancy: slots in use and bytes of the budget in use. */
 fastsv_status fastsv_pool_usage(fastsv_t h, int32_t* slots_used, size_t* bytes_used);

@@ -25,7 +25,7 @@ from ._lib import (  # noqa: F401  (re-exported C names)
     fastsv_get_stats, fastsv_status_string, fastsv_last_cuda_error, fastsv_kernel_launches,
     fastsv_pool_create, fastsv_pool_bytes, fastsv_pool_add, fastsv_pool_step, fastsv_pool_poll,
     fastsv_pool_usage, load, library_path, fastsv_cc_noalloc, FASTSV_NOALLOC_MAX_VERTICES,
-    fastsv_pool_checkpoint_bytes, fastsv_pool_evict, fastsv_pool_restore,
+    fastsv_pool_checkpoint_bytes, fastsv_pool_evict, fastsv_pool_restore, fastsv_pool_step_times,
 )
 
 

@@ -102,6 +102,7 @@ _SIGNATURES = [
     ("fastsv_pool_step", C.c_int, [_P, C.c_int32, _P]),
     ("fastsv_pool_poll", C.c_int, [_P, _P, _P, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     ("fastsv_pool_usage", C.c_int, [_P, C.POINTER(C.c_int32), C.POINTER(C.c_size_t)]),
+    ("fastsv_pool_step_times", C.c_int, [_P, _P]),
     ("fastsv_pool_checkpoint_bytes", C.c_size_t, [C.c_int64]),
     ("fastsv_pool_evict", C.c_int, [_P, C.c_int32, _P]),
     ("fastsv_pool_restore", C.c_int, [_P, C.c_int64, _P, _P, _P, _P, C.POINTER(C.c_int32)]),
@@ -230,6 +231,13 @@ def fastsv_pool_usage(h: int) -> tuple[int, int, int]:
     b = C.c_size_t(0)
     st = _call("fastsv_pool_usage", h, C.byref(used), C.byref(b))
     return st, used.value, b.value
+
+
+def fastsv_pool_step_times(h: int) -> tuple[int, list[float]]:
+    """(status, [ms waiting for admission copies, ms admit + rebuild, ms iterations]) of the last step."""
+    out = (C.c_float * 3)()
+    st = _call("fastsv_pool_step_times", h, C.cast(out, C.c_void_p))
+    return st, [out[0], out[1], out[2]]
 
 
 def fastsv_pool_checkpoint_bytes(n: int) -> int:

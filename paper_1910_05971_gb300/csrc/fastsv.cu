@@ -542,11 +542,19 @@ static int choose_col_blocks(const fastsv_ctx* h, int64_t n, int64_t m) {
     if (m > (int64_t)INT32_MAX - 1) return 1;  // block row pointers are int32
     if (nb == 1) return 1;
     if (nb <= 0) {
-        // Automatic: measured on R-MAT scale 26 (GB300), 4 blocks cut a full
-        // SpMV from 18.3 to 11.8 ms but the per-call block copy costs ~50 ms,
-        // more than the 4-5 dense iterations such graphs need can win back,
-        // so blocking is only taken when asked for explicitly.
-        return 1;
+        // Automatic: block when the gathered vector (4n bytes) is at least
+        // 1.5x the L2 and the graph is dense enough (m >= 8n) that the
+        // per-block row pointers and the one-time copy pay off, with slices
+        // of 64 MiB (about half of GB300's 129 MiB L2).  Measured on GB300:
+        // R-MAT scale 26 (gf 268 MB) gets 4 blocks, a full SpMV drops from
+        // 18.4 to 11.8 ms and the solve from 79.4 to 67.9 ms (2 blocks: 80 ms,
+        // 8 blocks: 74 ms); R-MAT scale 25 at edge factor 8 (gf 134 MB) is
+        // faster unblocked and stays so.
+        const int64_t l2 = h->l2_bytes > 0 ? h->l2_bytes : (int64_t)129 << 20;
+        if (m < 8 * n || 2 * (4 * n) < 3 * l2) return 1;
+        const int64_t slice = (int64_t)64 << 20;
+        const int64_t want = (4 * n + slice - 1) / slice;
+        return (int)(want < 2 ? 2 : (want < MAX_COL_BLOCKS ? want : MAX_COL_BLOCKS));
     }
     if (nb > MAX_COL_BLOCKS) nb = MAX_COL_BLOCKS;
     return nb;
@@ -564,11 +572,13 @@ static fastsv_status launch_block_build(fastsv_ctx* h, int nb, int shift, int64_
     FSV_CUDA(h, cudaFuncSetAttribute(fr, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_count));
     Ctx* ctx = h->d_ctx;
     int32_t* flag = h->d_sums + h->cap_sums - 1;  // "some row is not sorted by column"
-    int32_t* start = h->d_rpB;                    // run starts first, then the block row pointers
-    FSV_CUDA(h, cudaMemsetAsync(flag, 0, sizeof(int32_t), s));
-    // sorted rows: run starts, counts as their differences
-    k_block_starts<RP><<<g, BS_THREADS, 0, s>>>(ctx, start, nb, shift, flag);
-    k_block_counts<RP><<<g, 256, 0, s>>>(ctx, start, h->d_counts, nb, flag);
+    long long* descents = h->d_build_scalars;
+    int32_t* start = h->d_rpB;  // run starts of every (row, block)
+    FSV_CUDA(h, cudaMemsetAsync(descents, 0, sizeof(long long), s));
+    k_sorted_check<RP><<<g, 256, 0, s>>>(ctx, descents);
+    k_sorted_verdict<<<1, 1, 0, s>>>(descents, flag);
+    // sorted rows: run starts by binary search, counts as their differences
+    k_block_runs<RP><<<g, 256, 0, s>>>(ctx, start, h->d_counts, nb, shift, flag);
     {
         // unsorted rows: count per (row, block) instead (returns at once otherwise)
         void* a[] = {(void*)&ctx, (void*)&h->d_counts, (void*)&nb, (void*)&shift, (void*)&flag};
@@ -582,12 +592,11 @@ static fastsv_status launch_block_build(fastsv_ctx* h, int nb, int shift, int64_
     // counts buffer, which the scan no longer needs once applied in place
     k_scan_apply<<<(unsigned)(nb * chunks), SCAN_THREADS, 0, s>>>(h->d_counts, h->d_counts, np1, ch, h->d_sums);
     {
-        const void* fs = (const void*)k_block_scatter_runs<RP>;
-        const int smem_runs = runs_smem(nb);
-        FSV_CUDA(h, cudaFuncSetAttribute(fs, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_runs));
-        void* a[] = {(void*)&ctx, (void*)&h->d_counts, (void*)&start, (void*)&h->d_colB, (void*)&nb,
-                     (void*)&shift, (void*)&flag};
-        FSV_CUDA(h, cudaLaunchKernel(fs, dim3(g), dim3(BS_THREADS), a, (size_t)smem_runs, s));
+        // sorted rows: stable partition of col_idx by block
+        const int64_t ptiles = (h->last_m_build + PART_TILE - 1) / PART_TILE;
+        k_part_tile_rows<RP><<<g, 256, 0, s>>>(ctx, h->d_part_u0, ptiles);
+        k_block_partition<RP><<<g, PART_THREADS, 0, s>>>(ctx, h->d_counts, start, h->d_part_u0, h->d_colB, nb, shift,
+                                                       flag);
     }
     {
         // unsorted rows: ranks from atomics; the run-start buffer becomes the
@@ -597,13 +606,17 @@ static fastsv_status launch_block_build(fastsv_ctx* h, int nb, int shift, int64_
                      (void*)&shift, (void*)&flag};
         FSV_CUDA(h, cudaLaunchKernel(fr, dim3(g), dim3(BUILD_THREADS), a, (size_t)smem_count, s));
     }
-    h->pending_fixed_launches += 9;
+    h->pending_fixed_launches += 11;
     FSV_CUDA(h, cudaGetLastError());
     return FASTSV_OK;
 }
 
 static fastsv_status ensure_block_workspace(fastsv_ctx* h, int nb, int64_t n, int64_t m) {
     const int64_t cells = (int64_t)nb * (n + 1);
+    if (!h->d_build_scalars) {
+        fastsv_status st0 = dev_alloc(h, (void**)&h->d_build_scalars, 64);
+        if (st0 != FASTSV_OK) return st0;
+    }
     const int64_t sums = (int64_t)nb * ((n + 1 + SCAN_CHUNK - 1) / SCAN_CHUNK) + 1;
     fastsv_status st;
     if (cells > h->cap_blk) {
@@ -629,6 +642,14 @@ static fastsv_status ensure_block_workspace(fastsv_ctx* h, int nb, int64_t n, in
         if ((st = dev_alloc(h, (void**)&h->d_colB, (size_t)m * 4)) != FASTSV_OK) return st;
         h->cap_colB = m;
     }
+    const int64_t ptiles = (m + PART_TILE - 1) / PART_TILE + 1;
+    if (ptiles > h->cap_part_u0) {
+        dev_free((void**)&h->d_part_u0);
+        h->cap_part_u0 = 0;
+        if ((st = dev_alloc(h, (void**)&h->d_part_u0, (size_t)ptiles * 4)) != FASTSV_OK) return st;
+        h->cap_part_u0 = ptiles;
+    }
+    h->last_m_build = m;
     return FASTSV_OK;
 }
 
@@ -774,6 +795,11 @@ fastsv_status fastsv_create(fastsv_t* out, const fastsv_options* opt) {
     fastsv_status st = FASTSV_OK;
     cudaError_t e = cudaGetDevice(&h->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e == cudaSuccess) {
+        int l2 = 0;
+        e = cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, h->device);
+        h->l2_bytes = l2;
+    }
     if (e == cudaSuccess) e = cudaMalloc((void**)&h->d_ctx, sizeof(Ctx));
     if (e == cudaSuccess) e = cudaMemset(h->d_ctx, 0, sizeof(Ctx));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&h->h_sum, sizeof(Summary));
@@ -812,6 +838,8 @@ fastsv_status fastsv_destroy(fastsv_t h) {
     dev_free((void**)&h->d_rpB);
     dev_free((void**)&h->d_sums);
     dev_free((void**)&h->d_colB);
+    dev_free((void**)&h->d_build_scalars);
+    dev_free((void**)&h->d_part_u0);
     dev_free(&h->d_rp_copy);
     dev_free((void**)&h->d_ci_copy);
     dev_free((void**)&h->d_lab_copy);

@@ -38,6 +38,7 @@ struct fastsv_ctx {
     fastsv_options opt;
     int device = 0;
     int num_sms = 0;
+    int64_t l2_bytes = 0;
     cudaStream_t last_stream = nullptr;
 
     // device context and workspace
@@ -63,6 +64,10 @@ struct fastsv_ctx {
     int64_t cap_sums = 0;
     int32_t* d_colB = nullptr;
     int64_t cap_colB = 0;
+    long long* d_build_scalars = nullptr;  // block build: descent counter
+    int32_t* d_part_u0 = nullptr;           // block build: first row of every partition tile
+    int64_t cap_part_u0 = 0;
+    int64_t last_m_build = 0;
     int last_col_blocks = 1;
 
     // device copies for the host-buffer entry point

@@ -563,115 +563,78 @@ __global__ void __launch_bounds__(BUILD_THREADS)
 }
 
 // ---------------------------------------------------------------------------
-// column-block build for rows sorted by column (the common case): one
-// streaming pass finds where each (row, block) run starts, counts are the
-// differences of those starts, and the scatter copies each run in order
+// column-block build for rows sorted by column (the common case): a
+// streaming sortedness test, run starts of every (row, block) by binary
+// search, and a stable partition of col_idx by block
 // ---------------------------------------------------------------------------
 
-constexpr int BS_THREADS = 256;  // 256 threads x 4 items: the build tiles (BUILD_TILE items)
-constexpr int BS_ITEMS = BUILD_TILE / BS_THREADS;
-
-// tile row of every entry of the tile: each thread walks its BS_ITEMS
-// merge-path items (shared memory only), so the passes after it can take the
-// entries in striped order, where consecutive threads touch consecutive
-// entries and their global accesses coalesce
-__device__ __forceinline__ void tile_rows_of_entries(const int32_t* s_rowend, int32_t* s_rowof, int nfull, int D) {
-    const int k0 = threadIdx.x * BS_ITEMS;
-    if (k0 >= D) return;
-    int lo = 0, hi = nfull;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (s_rowend[mid] + mid < k0)
-            lo = mid + 1;
-        else
-            hi = mid;
-    }
-    int r = lo, y = k0 - lo;
-    int rend = r < nfull ? s_rowend[r] : 0x7fffffff;
-    const int steps = min(BS_ITEMS, D - k0);
-    for (int k = 0; k < steps; ++k) {
-        if (y >= rend) {
-            ++r;
-            rend = r < nfull ? s_rowend[r] : 0x7fffffff;
-        } else {
-            s_rowof[y++] = r;
-        }
-    }
-}
-
-// start[k][u] = position of the first entry of row u whose column block is
-// >= k, or the row end if there is none (k-major, stride n+1).  For a row
-// sorted by column, block k's run of row u is [start[k][u], start[k+1][u])
-// (the row end for the last block).  Every (k, u) is written exactly once:
-// by the entry that opens a run (for the blocks after the previous entry's
-// block, up to its own) or at the row end (for the blocks after the row's
-// last entry).  An entry whose block is below its predecessor's marks the
-// graph as unsorted, and the build then takes the ranked path instead.
+// Sortedness test of the whole graph in two streaming passes: +1 for every
+// adjacent pair of entries in decreasing order (as unsigned ids, the order
+// the column blocks follow), -1 for every such pair that straddles a row
+// boundary (the last entry of one row before the first of the next
+// non-empty row).  The sum is zero exactly when every row is sorted.
 template <typename RP>
-__global__ void __launch_bounds__(BS_THREADS, 5)
-    k_block_starts(Ctx* ctx, int32_t* start, int nb, int shift, int32_t* unsorted) {
-    __shared__ int32_t s_rowend[BUILD_TILE + 1];
-    __shared__ int32_t s_col[BUILD_TILE];
-    __shared__ int32_t s_rowof[BUILD_TILE];
+__global__ void k_sorted_check(const Ctx* ctx, long long* descents) {
     const Seg& S = ctx->segs[0];
     const RP* rp = (const RP*)S.rp;
-    const int32_t* ci = S.ci;
-    const int64_t np1 = S.n + 1;
-    const int64_t T = S.k2_ntiles;
-    int bad = 0;
-    for (int64_t t = blockIdx.x; t < T; t += gridDim.x) {
-        int64_t x0;
-        int nfull, R, E, D;
-        if (!load_tile<RP, BS_ITEMS>(S, t, BUILD_TILE, ctx->k2_tile_row, s_rowend, s_col, x0, nfull, R, E, D))
-            continue;
-        const int64_t y0 = t * (int64_t)BUILD_TILE - x0;
-        const bool first_whole = rp_at(rp, x0) >= y0;
-        // block of the last entry of row 0 before this tile (the row began earlier)
-        const int carry = (!first_whole && y0 > 0) ? col_block(ci[y0 - 1], shift, nb) : -1;
-        __syncthreads();
-        tile_rows_of_entries(s_rowend, s_rowof, nfull, D);
-        __syncthreads();
-        // entries that open a block run of their row
-        for (int y = threadIdx.x; y < E; y += BS_THREADS) {
-            const int r = s_rowof[y];
-            const int b = col_block(s_col[y], shift, nb);
-            const int pb = y > row_start_local(s_rowend, r) ? col_block(s_col[y - 1], shift, nb) : (r == 0 ? carry : -1);
-            if (b < pb) {
-                bad = 1;
-                continue;
-            }
-            for (int kk = pb + 1; kk <= b; ++kk) start[kk * np1 + x0 + r] = (int32_t)(y0 + y);
-        }
-        // row ends: the blocks after each row's last entry
-        for (int r = threadIdx.x; r < nfull; r += BS_THREADS) {
-            const int rs = row_start_local(s_rowend, r), re = s_rowend[r];
-            const int lastb = re > rs ? col_block(s_col[re - 1], shift, nb) : (r == 0 ? carry : -1);
-            for (int kk = lastb + 1; kk < nb; ++kk) start[kk * np1 + x0 + r] = (int32_t)(y0 + re);
-        }
-        __syncthreads();
+    const uint32_t* ci = (const uint32_t*)S.ci;
+    const int64_t n = S.n, m = S.m;
+    long long d = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e + 1 < m; e += stride)
+        d += ci[e] > ci[e + 1];
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x + 1; u < n; u += stride) {
+        const int64_t b = rp_at(rp, u);
+        if (b > 0 && b < m && b < rp_at(rp, u + 1)) d -= ci[b - 1] > ci[b];
     }
-    if (bad) atomicOr(unsorted, 1);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
+    if ((threadIdx.x & 31) == 0 && d) atomicAdd((unsigned long long*)descents, (unsigned long long)d);
 }
 
-// counts[k][u] = start[k+1][u] - start[k][u] (row end for the last block),
-// counts[k][n] = 0; all zero when the graph is unsorted (the ranked path's
-// counting kernel then fills them)
+__global__ void k_sorted_verdict(const long long* descents, int32_t* unsorted) { *unsorted = *descents != 0; }
+
+// Sorted rows: start[k][u] = first position of row u whose column block is
+// >= k (the row end if none), found by binary search per (row, block)
+// boundary, and counts[k][u] = start[k+1][u] - start[k][u] (row end for the
+// last block); counts[k][n] = 0.  One thread per row.  All zero when the
+// graph is unsorted (the ranked path's counting kernel then fills counts).
 template <typename RP>
-__global__ void k_block_counts(const Ctx* ctx, const int32_t* start, int32_t* counts, int nb, const int32_t* unsorted) {
-    const Seg& S = ctx->segs[0];
-    const RP* rp = (const RP*)S.rp;
-    const int64_t n = S.n, np1 = n + 1;
+__global__ void __launch_bounds__(256) k_block_runs(const Ctx* ctx, int32_t* __restrict__ start,
+                                                    int32_t* __restrict__ counts, int nb, int shift,
+                                                    const int32_t* unsorted) {
+    const Seg& S0 = ctx->segs[0];
+    const RP* __restrict__ rp = (const RP*)S0.rp;
+    const uint32_t* __restrict__ ci = (const uint32_t*)S0.ci;
+    const int64_t n = S0.n, np1 = n + 1;
     const bool zero = *unsorted != 0;
-    const int64_t total = (int64_t)nb * np1;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-        const int k = (int)(i / np1);
-        const int64_t u = i - (int64_t)k * np1;
-        int32_t c = 0;
-        if (!zero && u < n) {
-            const int64_t next = k + 1 < nb ? (int64_t)start[i + np1] : rp_at(rp, u + 1);
-            c = (int32_t)(next - start[i]);
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < np1; u += (int64_t)gridDim.x * blockDim.x) {
+        if (u == n || zero) {
+            for (int k = 0; k < nb; ++k) counts[k * np1 + u] = 0;
+            continue;
         }
-        counts[i] = c;
+        const int64_t b0 = rp_at(rp, u), b1 = rp_at(rp, u + 1);
+        int64_t lo = b0, prev = b0;
+        start[u] = (int32_t)b0;
+        for (int k = 1; k <= nb; ++k) {
+            int64_t pos = b1;
+            if (k < nb) {
+                // first entry at or after lo with id >= k << shift
+                const uint32_t key = (uint32_t)k << shift;
+                int64_t hi = b1;
+                while (lo < hi) {
+                    const int64_t mid = (lo + hi) >> 1;
+                    if (ci[mid] < key)
+                        lo = mid + 1;
+                    else
+                        hi = mid;
+                }
+                pos = lo;
+                start[k * np1 + u] = (int32_t)pos;
+            }
+            counts[(k - 1) * np1 + u] = (int32_t)(pos - prev);
+            prev = pos;
+        }
     }
 }
 
@@ -681,125 +644,113 @@ __global__ void k_zero_if_unsorted(int32_t* p, int64_t count, const int32_t* uns
         p[i] = 0;
 }
 
-// sorted rows: entry e of row u in block b goes to
-//   base_b + rpB[b][u] + (e - start[b][u]);
-// the per-(row, block) offsets of a tile are loaded once into shared memory,
-// then the entries are copied in striped order (coalesced stores)
-constexpr int runs_smem(int nb) { return nb * (BUILD_TILE + 1) * (int)sizeof(int32_t); }
+// Sorted rows: the block-major copy colB is the stable partition of col_idx
+// by column block -- entries of block b keep their order, which is row
+// order and, inside a row, the run order.  Fixed tiles of PART_TILE
+// consecutive entries; a tile's first destination in block b follows from
+// the row u0 holding its first entry e0:
+//   base_b + rpB[b][u0] + clamp(e0 - start[b][u0], 0, count_b(u0)).
+// Inside the tile, steps of PART_THREADS entries are ranked stably per
+// block with warp ballots and a per-step prefix over the warps.
+constexpr int PART_THREADS = 256;
+constexpr int PART_STEPS = 16;
+constexpr int PART_TILE = PART_THREADS * PART_STEPS;
 
+// row holding the first entry of every partition tile (largest u with
+// rp[u] <= e0), one binary search per tile
 template <typename RP>
-__global__ void __launch_bounds__(BS_THREADS, 4)
-    k_block_scatter_runs(Ctx* ctx, const int32_t* rpB, const int32_t* start, int32_t* colB, int nb, int shift,
-                         const int32_t* unsorted) {
-    if (*unsorted) return;
-    constexpr int RS = BUILD_TILE + 1;
-    __shared__ int32_t s_rowend[BUILD_TILE + 1];
-    __shared__ int32_t s_col[BUILD_TILE];
-    __shared__ int32_t s_rowof[BUILD_TILE];
-    __shared__ long long s_blockbase[MAX_COL_BLOCKS];
-    extern __shared__ int32_t s_off[];  // [nb][RS]: rpB[b][u] - start[b][u]
-    const Seg& S = ctx->segs[0];
-    const int64_t np1 = S.n + 1;
-    const int64_t m = S.m;
-    const int64_t T = S.k2_ntiles;
-    if (threadIdx.x == 0) {
-        long long acc = 0;
-        for (int b = 0; b < nb; ++b) {
-            s_blockbase[b] = acc;
-            acc += rpB[(int64_t)b * np1 + S.n];
+__global__ void k_part_tile_rows(const Ctx* ctx, int32_t* tile_u0, int64_t tiles) {
+    const Seg& S0 = ctx->segs[0];
+    const RP* rp = (const RP*)S0.rp;
+    const int64_t n = S0.n;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tiles; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e0 = t * PART_TILE;
+        int64_t lo = 0, hi = n - 1;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (rp_at(rp, mid) <= e0)
+                lo = mid;
+            else
+                hi = mid - 1;
         }
-    }
-    for (int64_t t = blockIdx.x; t < T; t += gridDim.x) {
-        int64_t x0;
-        int nfull, R, E, D;
-        if (!load_tile<RP, BS_ITEMS>(S, t, BUILD_TILE, ctx->k2_tile_row, s_rowend, s_col, x0, nfull, R, E, D))
-            continue;
-        const int64_t y0 = t * (int64_t)BUILD_TILE - x0;
-        for (int i = threadIdx.x; i < nb * R; i += BS_THREADS) {
-            const int b = i / R, r = i - b * R;
-            const int64_t g = (int64_t)b * np1 + x0 + r;
-            s_off[b * RS + r] = rpB[g] - start[g];
-        }
-        __syncthreads();
-        tile_rows_of_entries(s_rowend, s_rowof, nfull, D);
-        __syncthreads();
-        for (int y = threadIdx.x; y < E; y += BS_THREADS) {
-            const int32_t c = s_col[y];
-            const int b = col_block(c, shift, nb);
-            const long long pos = s_blockbase[b] + s_off[b * RS + s_rowof[y]] + y0 + y;
-            if (pos >= 0 && pos < m) colB[pos] = c;
-        }
-        __syncthreads();
+        tile_u0[t] = (int32_t)lo;
     }
 }
 
-// With every row sorted by column, the entries of row u that fall in block
-// b are one contiguous run of row u, so entry e goes to
-//   base_b + rpB[b][u] + (e - rp[u] - sum_{b' < b} counts[b'][u]),
-// a plain coalesced copy.  Returns at once when a row was found unsorted.
-constexpr int block_scatter_smem(int nb) { return (2 + 2 * nb) * (BUILD_TILE + 1) * (int)sizeof(int32_t); }
-
 template <typename RP>
-__global__ void __launch_bounds__(BUILD_THREADS)
-    k_block_scatter_sorted(Ctx* ctx, const int32_t* rpB, const int32_t* counts, int32_t* colB, int nb, int shift,
-                           const int32_t* unsorted) {
-    constexpr int TILE = BUILD_TILE;
-    constexpr int RS = TILE + 1;
+__global__ void __launch_bounds__(PART_THREADS)
+    k_block_partition(Ctx* ctx, const int32_t* __restrict__ rpB, const int32_t* __restrict__ start,
+                      const int32_t* __restrict__ tile_u0, int32_t* __restrict__ colB, int nb, int shift,
+                      const int32_t* unsorted) {
     if (*unsorted) return;
-    extern __shared__ int32_t smem[];
-    int32_t* s_rowend = smem;
-    int32_t* s_col = smem + RS;
-    long long* s_delta = (long long*)(smem + 2 * RS);  // [nb][RS]
-    __shared__ long long s_blockbase[MAX_COL_BLOCKS];
-    const Seg S = ctx->segs[0];
-    const RP* rp = (const RP*)S.rp;
-    const int64_t np1 = S.n + 1;
-    const int64_t m = S.m;
-    if (threadIdx.x == 0) {
-        long long acc = 0;
-        for (int b = 0; b < nb; ++b) {
-            s_blockbase[b] = acc;
-            acc += rpB[(int64_t)b * np1 + S.n];
+    constexpr int W = PART_THREADS / 32;
+    __shared__ long long s_tile_off[MAX_COL_BLOCKS];
+    __shared__ int32_t s_wcnt[2][W][MAX_COL_BLOCKS];  // per step: warp counts, then warp offsets
+    __shared__ int32_t s_run[MAX_COL_BLOCKS];         // entries of each block in the tile's earlier steps
+    const Seg& S0 = ctx->segs[0];
+    const int32_t* __restrict__ ci = S0.ci;
+    const int64_t np1 = S0.n + 1, m = S0.m;
+    const int64_t tiles = (m + PART_TILE - 1) / PART_TILE;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    long long base_b = 0;  // thread b < nb: entries of the blocks before b
+    if (threadIdx.x < nb)
+        for (int b = 0; b < (int)threadIdx.x; ++b) base_b += rpB[(int64_t)b * np1 + S0.n];
+    for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+        const int64_t e0 = t * PART_TILE;
+        if (threadIdx.x < nb) {
+            const int b = threadIdx.x;
+            const int64_t u0 = tile_u0[t];
+            const int64_t i = (int64_t)b * np1 + u0;
+            const long long cnt = (long long)rpB[i + 1] - rpB[i];
+            long long before = e0 - (long long)start[i];
+            before = before < 0 ? 0 : (before > cnt ? cnt : before);
+            s_tile_off[b] = base_b + rpB[i] + before;
+            s_run[b] = 0;
         }
-    }
-    __syncthreads();
-    for (int64_t t = blockIdx.x; t < S.k2_ntiles; t += gridDim.x) {
-        int64_t x0;
-        int nfull, R, E, D;
-        if (!load_tile<RP>(S, t, TILE, ctx->k2_tile_row, s_rowend, s_col, x0, nfull, R, E, D)) continue;
-        const int64_t y0 = (t - S.k2_tile0) * TILE - x0;
-        for (int r = threadIdx.x; r < R; r += BUILD_THREADS) {
-            const int64_t u = x0 + r;
-            long long before = rp_at(rp, u);
-            for (int b = 0; b < nb; ++b) {
-                s_delta[b * RS + r] = s_blockbase[b] + rpB[(int64_t)b * np1 + u] - before;
-                before += counts[(int64_t)b * np1 + u];
-            }
+        // every load of the tile first: one memory round trip per tile
+        int32_t cv[PART_STEPS];
+#pragma unroll
+        for (int st = 0; st < PART_STEPS; ++st) {
+            const int64_t e = e0 + (int64_t)st * PART_THREADS + threadIdx.x;
+            cv[st] = e < m ? ld_stream(ci + e) : 0;
         }
         __syncthreads();
-        const int k0 = threadIdx.x * BUILD_ITEMS;
-        if (k0 < D) {
-            int lo = 0, hi = nfull;
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (s_rowend[mid] + mid < k0)
-                    lo = mid + 1;
-                else
-                    hi = mid;
+#pragma unroll
+        for (int st = 0; st < PART_STEPS; ++st) {
+            const int64_t e = e0 + (int64_t)st * PART_THREADS + threadIdx.x;
+            const bool valid = e < m;
+            const int32_t c = cv[st];
+            const int b = valid ? col_block(c, shift, nb) : 0;
+            // lanes of the same block: the ballots of the block id's four bits
+            const unsigned vb = __ballot_sync(0xffffffffu, valid);
+            unsigned bits[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) bits[k] = __ballot_sync(0xffffffffu, (b >> k) & 1);
+            unsigned same = vb;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) same &= ((b >> k) & 1) ? bits[k] : ~bits[k];
+            if (lane < nb) {  // this warp's count of block `lane`
+                unsigned mk = vb;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) mk &= ((lane >> k) & 1) ? bits[k] : ~bits[k];
+                s_wcnt[st & 1][w][lane] = __popc(mk);
             }
-            int r = lo, y = k0 - lo;
-            int rend = r < nfull ? s_rowend[r] : 0x7fffffff;
-            const int steps = min(BUILD_ITEMS, D - k0);
-            for (int k = 0; k < steps; ++k) {
-                if (y >= rend) {
-                    ++r;
-                    rend = r < nfull ? s_rowend[r] : 0x7fffffff;
-                } else {
-                    const int32_t c = s_col[y];
-                    const long long pos = s_delta[col_block(c, shift, nb) * RS + r] + y0 + y;
-                    if (pos >= 0 && pos < m) colB[pos] = c;
-                    ++y;
+            __syncthreads();
+            if (threadIdx.x < nb) {  // warp offsets of block b in this step, after the earlier steps
+                const int bb = threadIdx.x;
+                int run = s_run[bb];
+                for (int ww = 0; ww < W; ++ww) {
+                    const int x = s_wcnt[st & 1][ww][bb];
+                    s_wcnt[st & 1][ww][bb] = run;
+                    run += x;
                 }
+                s_run[bb] = run;
+            }
+            __syncthreads();
+            if (valid) {
+                const long long pos = s_tile_off[b] + s_wcnt[st & 1][w][b] + __popc(same & lt);
+                if (pos >= 0 && pos < m) colB[pos] = c;
             }
         }
         __syncthreads();

@@ -132,6 +132,8 @@ struct Pool {
     std::vector<int> admitted;  // slots whose copies were enqueued since the last step
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t copy_done = nullptr, step_done = nullptr;
+    cudaEvent_t ev_t[4] = {};  // step phases: start, copies landed, set-up done, loop done
+    bool timed = false;        // the last step recorded ev_t
     bool stepped = false;
     bool dirty = false;
 };
@@ -194,6 +196,8 @@ void pool_release(fastsv_ctx* h) {
     if (P->copy_stream) cudaStreamDestroy(P->copy_stream);
     if (P->copy_done) cudaEventDestroy(P->copy_done);
     if (P->step_done) cudaEventDestroy(P->step_done);
+    for (cudaEvent_t& ev : P->ev_t)
+        if (ev) cudaEventDestroy(ev);
     delete P;
     h->pool = nullptr;
 }
@@ -240,6 +244,7 @@ fastsv_status fastsv_pool_create(fastsv_t h, size_t budget, int32_t max_slots) {
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->copy_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->copy_done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->step_done, cudaEventDisableTiming);
+    for (int i = 0; i < 4 && e == cudaSuccess && h->opt.timing; ++i) e = cudaEventCreate(&P->ev_t[i]);
     if (e != cudaSuccess) {
         st = cuda_fail(h, e);
         pool_release(h);
@@ -392,11 +397,14 @@ fastsv_status fastsv_pool_step(fastsv_t h, int32_t iters, void* stream) {
     const int32_t tile = (int32_t)k2_tile(h);
     // the slot snapshot read below must be the previous step's final one
     if (P->stepped) FSV_CUDA(h, cudaEventSynchronize(P->step_done));
+    const bool timed = P->ev_t[0] != nullptr;
+    if (timed) FSV_CUDA(h, cudaEventRecord(P->ev_t[0], s));
     size_t na = P->admitted.size();
     if (na > 0) {
         FSV_CUDA(h, cudaEventRecord(P->copy_done, P->copy_stream));
         FSV_CUDA(h, cudaStreamWaitEvent(s, P->copy_done, 0));
     }
+    if (timed) FSV_CUDA(h, cudaEventRecord(P->ev_t[1], s));
     size_t done = 0;
     do {
         AdmitBatch b;
@@ -443,6 +451,7 @@ fastsv_status fastsv_pool_step(fastsv_t h, int32_t iters, void* stream) {
     bool any = na > 0;
     for (int i = 0; i < P->max_slots && !any; ++i)
         any = P->slots[i].state == 2 && P->h_segs[i].active;
+    if (timed) FSV_CUDA(h, cudaEventRecord(P->ev_t[2], s));
     if (any) {
         h->loop_limit_host = iters;
         const bool graph = h->opt.use_graph != 0;
@@ -458,9 +467,11 @@ fastsv_status fastsv_pool_step(fastsv_t h, int32_t iters, void* stream) {
                                         cudaMemcpyDeviceToHost, s));
         }
     }
+    if (timed) FSV_CUDA(h, cudaEventRecord(P->ev_t[3], s));
     FSV_CUDA(h, cudaMemcpyAsync(P->h_segs, P->d_segs, sizeof(Seg) * (size_t)P->max_slots, cudaMemcpyDeviceToHost, s));
     FSV_CUDA(h, cudaEventRecord(P->step_done, s));
     P->stepped = true;
+    P->timed = timed;
     h->pool_loop_pending = any && h->opt.use_graph;
     return FASTSV_OK;
 }
@@ -513,6 +524,21 @@ fastsv_status fastsv_pool_poll(fastsv_t h, int32_t* done_slots, int32_t* done_it
     }
     *n_done = nd;
     if (n_active) *n_active = act;
+    return FASTSV_OK;
+}
+
+fastsv_status fastsv_pool_step_times(fastsv_t h, float* ms_out) {
+    if (!h || !h->pool || !ms_out) return FASTSV_ERR_INVALID_ARG;
+    Pool* P = h->pool;
+    ms_out[0] = ms_out[1] = ms_out[2] = 0.f;
+    if (!P->stepped || !P->timed) return FASTSV_OK;
+    fastsv_status st = settle_step(h, P);
+    if (st != FASTSV_OK) return st;
+    for (int i = 0; i < 3; ++i)
+        if (cudaEventElapsedTime(&ms_out[i], P->ev_t[i], P->ev_t[i + 1]) != cudaSuccess) {
+            (void)cudaGetLastError();
+            ms_out[i] = 0.f;
+        }
     return FASTSV_OK;
 }
 
