@@ -218,7 +218,8 @@ size_t fastsv_pool_bytes(int64_t n, int64_t m);
  * memory, pinned recommended, must stay valid until the graph is harvested),
  * labels_host int32[n] host memory that receives the labels when the slot is
  * harvested.  The copies to the device are enqueued on the pool's copy
- * stream.  *slot_out receives the slot id.
+ * stream and may be issued while a step runs (they overlap it; the graph
+ * joins at the next step).  *slot_out receives the slot id.
  * Errors: FASTSV_ERR_FULL if no slot or not enough budget is free now (try
  * again after harvesting), FASTSV_ERR_INVALID_ARG if it can never fit.
  */

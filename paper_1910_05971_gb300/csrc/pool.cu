@@ -130,7 +130,8 @@ struct Pool {
     int max_slots = 0;
     std::vector<Slot> slots;
     std::vector<int> admitted;  // slots whose copies were enqueued since the last step
-    cudaStream_t copy_stream = nullptr;
+    cudaStream_t copy_stream = nullptr;  // admissions (host to device), may run during a step
+    cudaStream_t out_stream = nullptr;   // harvests (labels to host)
     cudaEvent_t copy_done = nullptr, step_done = nullptr;
     cudaEvent_t ev_t[4] = {};  // step phases: start, copies landed, set-up done, loop done
     bool timed = false;        // the last step recorded ev_t
@@ -186,6 +187,7 @@ void pool_release(fastsv_ctx* h) {
     if (!P) return;
     if (P->step_done) cudaEventSynchronize(P->step_done);
     if (P->copy_stream) cudaStreamSynchronize(P->copy_stream);
+    if (P->out_stream) cudaStreamSynchronize(P->out_stream);
     if (P->d_ctx) cudaFree(P->d_ctx);
     if (P->d_segs) cudaFree(P->d_segs);
     if (P->h_segs) cudaFreeHost(P->h_segs);
@@ -194,6 +196,7 @@ void pool_release(fastsv_ctx* h) {
     if (P->d_k3_seg) cudaFree(P->d_k3_seg);
     if (P->arena) cudaFree(P->arena);
     if (P->copy_stream) cudaStreamDestroy(P->copy_stream);
+    if (P->out_stream) cudaStreamDestroy(P->out_stream);
     if (P->copy_done) cudaEventDestroy(P->copy_done);
     if (P->step_done) cudaEventDestroy(P->step_done);
     for (cudaEvent_t& ev : P->ev_t)
@@ -242,6 +245,7 @@ fastsv_status fastsv_pool_create(fastsv_t h, size_t budget, int32_t max_slots) {
     if (e == cudaSuccess) e = cudaMemset(P->d_segs, 0, sizeof(Seg) * (size_t)max_slots);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&P->h_segs, sizeof(Seg) * (size_t)max_slots);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->copy_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->out_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->copy_done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->step_done, cudaEventDisableTiming);
     for (int i = 0; i < 4 && e == cudaSuccess && h->opt.timing; ++i) e = cudaEventCreate(&P->ev_t[i]);
@@ -504,7 +508,7 @@ fastsv_status fastsv_pool_poll(fastsv_t h, int32_t* done_slots, int32_t* done_it
         if (S.n > 0) {
             size_t o = align_up((size_t)(S.n + 1) * 4) + align_up((size_t)(S.m > 0 ? S.m : 1) * 4);
             cudaError_t e = cudaMemcpyAsync(S.labels_host, P->arena + S.off + o, (size_t)S.n * 4,
-                                            cudaMemcpyDeviceToHost, P->copy_stream);
+                                            cudaMemcpyDeviceToHost, P->out_stream);
             if (e != cudaSuccess) return cuda_fail(h, e);
         }
         done_slots[nd] = i;
@@ -513,7 +517,9 @@ fastsv_status fastsv_pool_poll(fastsv_t h, int32_t* done_slots, int32_t* done_it
         harvested.push_back(i);
     }
     if (!harvested.empty()) {
-        cudaError_t e = cudaStreamSynchronize(P->copy_stream);
+        // admission copies of graphs added since the last step may still be
+        // running on the copy stream: harvests wait only for their own copies
+        cudaError_t e = cudaStreamSynchronize(P->out_stream);
         if (e != cudaSuccess) return cuda_fail(h, e);
         for (int i : harvested) {
             Slot& S = P->slots[i];

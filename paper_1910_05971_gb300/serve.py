@@ -6,7 +6,9 @@ Requests (CSR graphs in host memory) arrive on any thread through
   1. admit queued requests in arrival order while the pool has a free slot
      and enough of its HBM budget (a request that can never fit is failed);
   2. run ``iters_per_step`` FastSV iterations over every resident graph
-     (``fastsv_pool_step``: one device-side loop over all slots);
+     (``fastsv_pool_step``: one device-side loop over all slots), admitting
+     the requests that arrive meanwhile so that their copies to the device
+     overlap the step;
   3. harvest graphs that reached their early termination (Section 3.4 of the
      paper) -- their labels are copied to host memory and their slot and
      memory are freed for the next admissions.
@@ -266,6 +268,9 @@ class Server:
                     for r in self._resident.values():
                         r.resident_steps += 1
                     with self._cv:
+                        # requests that arrived meanwhile start copying to the
+                        # device while the step runs; they join the next one
+                        self._admit()
                         if self._queue:
                             self._queue[0].blocked_steps += 1
                     done, _ = self.backend.poll()
