@@ -207,7 +207,9 @@ int64_t fastsv_kernel_launches(fastsv_t h);
  * not depend on what else is in the pool.
  */
 
-/* Create the handle's pool (one per handle). */
+/* Create the handle's pool (one per handle).  Allocates the arena and writes
+ * it once (so that later host-to-device copies into it run at full speed);
+ * synchronises the device. */
 fastsv_status fastsv_pool_create(fastsv_t h, size_t hbm_budget_bytes, int32_t max_slots);
 
 /* Bytes of pool memory a graph with n vertices and m directed entries uses. */

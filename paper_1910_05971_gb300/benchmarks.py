@@ -122,6 +122,22 @@ def run_batched(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+def _warm_host_buffers(torch, pinned):
+    """Copy every pinned trace buffer to the device once before the timed
+    runs: the first device transfer out of a freshly pinned host buffer was
+    measured at ~22 GB/s against ~210 GB/s for later ones, which would
+    otherwise penalise whichever arm runs first.  Both arms then read the
+    same, already transferred buffers (a server's long-lived staging
+    buffers)."""
+    biggest = max(max(rp.numel(), ci.numel()) for rp, ci, _ in pinned)
+    dst = torch.empty(biggest, dtype=torch.int32, device="cuda")
+    for rp, ci, _ in pinned:
+        dst[:rp.numel()].copy_(rp, non_blocking=True)
+        dst[:ci.numel()].copy_(ci, non_blocking=True)
+    torch.cuda.synchronize()
+    del dst
+
+
 def run_serve(args, rank, world, local_rank):
     import torch
 
@@ -157,6 +173,7 @@ def run_serve(args, rank, world, local_rank):
     for f in [srv.submit(reqs[i][0], reqs[i][1]) for i in range(min(4, R))]:
         f.result()
     srv.completed.clear()
+    _warm_host_buffers(torch, pinned)
     launches0 = srv.backend.kernel_launches()
     futs = [None] * R
     start = time.perf_counter()
