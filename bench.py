@@ -194,6 +194,8 @@ def main():
                     help="variants mode: comma-separated workloads")
     ap.add_argument("--graphs", type=int, default=4096, help="batched mode: number of graphs")
     ap.add_argument("--requests", type=int, default=256, help="serve mode: trace prefix length")
+    ap.add_argument("--batch-sparse-div", type=int, default=0,
+                    help="batched/serve modes: per-graph sparse iterations threshold (0 = off)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -55,7 +55,7 @@ class FastSV:
     def __init__(self, rowptr_bits: int = 64, mode: int = FASTSV_MODE_SYNC, max_iters: int = 4096,
                  validate: int = 0, use_graph: bool = True, k2_items: int = 8, grid_ctas_per_sm: int = 0,
                  l2_persist: bool = False, timing: bool = True, fail_alloc_after: int = 0, col_blocks: int = 0,
-                 k2_threads: int = 256, sparse_div: int = 2, variant: int = 0):
+                 k2_threads: int = 256, sparse_div: int = 2, variant: int = 0, batch_sparse_div: int = 0):
         _torch()
         o = fastsv_default_options()
         o.rowptr_bits = rowptr_bits
@@ -72,6 +72,7 @@ class FastSV:
         o.k2_threads = k2_threads
         o.sparse_div = sparse_div
         o.variant = variant
+        o.batch_sparse_div = batch_sparse_div
         self.options = o
         self.h = fastsv_create(o)
 

@@ -49,7 +49,8 @@ class fastsv_options(C.Structure):
         ("k2_threads", C.c_int32),
         ("sparse_div", C.c_int32),
         ("variant", C.c_int32),
-        ("reserved", C.c_int32 * 2),
+        ("batch_sparse_div", C.c_int32),
+        ("reserved", C.c_int32 * 1),
     ]
 
 

@@ -54,7 +54,7 @@ def run_batched(args, rank, world, local_rank):
     _log(f"[bench] batch of {G} graphs, n={N} m={M}, generated in {time.time() - t0:.1f}s")
     d = {k: torch.from_numpy(getattr(batch, k)).cuda() for k in ("vtx_off", "edge_off", "row_ptr", "col_idx")}
     stream = torch.cuda.current_stream()
-    solver = fsv.FastSV(rowptr_bits=32, k2_items=args.k2_items)
+    solver = fsv.FastSV(rowptr_bits=32, k2_items=args.k2_items, batch_sparse_div=args.batch_sparse_div)
     labels = torch.empty(N, dtype=torch.int32, device="cuda")
     iters = torch.empty(G, dtype=torch.int32, device="cuda")
     for _ in range(args.warmup):
@@ -168,7 +168,8 @@ def run_serve(args, rank, world, local_rank):
     arrivals = tr["t"] - tr["t"][0]
 
     # continuous batching
-    srv = Server(hbm_budget_bytes=120 << 30, max_slots=1024, iters_per_step=2, k2_items=args.k2_items)
+    srv = Server(hbm_budget_bytes=120 << 30, max_slots=1024, iters_per_step=2, k2_items=args.k2_items,
+                 batch_sparse_div=args.batch_sparse_div)
     # warm-up: a few requests through the server
     for f in [srv.submit(reqs[i][0], reqs[i][1]) for i in range(min(4, R))]:
         f.result()
@@ -228,7 +229,8 @@ def run_serve(args, rank, world, local_rank):
         "dtype": "int32", "data": "synthetic",
         "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
         "config": {"workload": f"serve_trace_prefix_{R}", "requests": R, "m_directed_total": int(m_tot),
-                   "rate_per_s": 2000, "hbm_budget_gb": 120, "iters_per_step": 2, "seed": 5},
+                   "rate_per_s": 2000, "hbm_budget_gb": 120, "iters_per_step": 2, "seed": 5,
+                   "batch_sparse_div": args.batch_sparse_div},
         "per_graph_plain_launches": {"graphs_per_s": base_gps, "p50_ms": float(np.percentile(base_lat, 50) * 1e3),
                                      "p99_ms": float(np.percentile(base_lat, 99) * 1e3)},
         "identical_labels_and_iterations": bool(same), "gpu_launches": int(launches), "clocks": clocks}),

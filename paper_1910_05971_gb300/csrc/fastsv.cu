@@ -86,7 +86,9 @@ fastsv_status ensure_workspace(fastsv_ctx* h, int64_t n, int64_t k2, int64_t k3,
         h->cap_n = 0;
         int64_t c = n;
         for (auto a : arrays) {
-            if ((st = dev_alloc(h, (void**)a, (size_t)c * 4)) != FASTSV_OK) {
+            // the frontier holds (graph, vertex) pairs: two int32 per vertex
+            const size_t bytes = (size_t)c * 4 * (a == &h->d_frontier ? 2 : 1);
+            if ((st = dev_alloc(h, (void**)a, bytes)) != FASTSV_OK) {
                 for (auto b : arrays) dev_free((void**)b);
                 return st;
             }
@@ -271,7 +273,7 @@ fastsv_status run_loop(fastsv_ctx* h, Ctx* ctx, int rp64_orig, int rp64_dense, i
     int no_cond = 0;
     int32_t limit = h->loop_limit_host;
     fastsv_status rc = FASTSV_OK;
-    int32_t mode = 0;
+    int32_t mode = MODE_DENSE;
     for (;;) {
         void* a_begin[] = {(void*)&ctx, (void*)&none, (void*)&no_cond};
         void* a_ctx[] = {(void*)&ctx};
@@ -306,12 +308,11 @@ fastsv_status run_loop(fastsv_ctx* h, Ctx* ctx, int rp64_orig, int rp64_dense, i
         cudaEventElapsedTime(&b, e[1], e[2]);
         cudaEventElapsedTime(&c, e[2], e[3]);
         cudaEventElapsedTime(&d, e[3], e[4]);
-        if (mode == 0) {
+        if (mode & MODE_DENSE) {
             t_spmv += a;
             ++dense;
-        } else {
-            t_push += b;
         }
+        if (mode & MODE_PUSH) t_push += b;
         t_hook += c;
         t_k3 += d;
         ++iters;
@@ -689,7 +690,7 @@ static fastsv_status solve_single(fastsv_ctx* h, int64_t n, int64_t m, const voi
     prm.gf = variant == 1 ? h->d_p : h->d_gf;  // sv1's SpMV gathers parents, not grandparents
     prm.mngf = h->d_mngf;
     prm.frontier = h->d_frontier;
-    prm.sparse_max_deg = (plain && h->opt.sparse_div > 0) ? m / h->opt.sparse_div : -1;
+    prm.sparse_div = (plain && h->opt.sparse_div > 0) ? h->opt.sparse_div : 0;
     prm.n = n;
     prm.m = m;
     prm.k2_tile = (int32_t)tile0;
@@ -789,6 +790,7 @@ fastsv_status fastsv_create(fastsv_t* out, const fastsv_options* opt) {
     if (o.max_iters < 1 || o.max_iters > (1 << 30)) return FASTSV_ERR_INVALID_ARG;
     if (o.validate < 0 || o.validate > 2) return FASTSV_ERR_INVALID_ARG;
     if (o.variant < 0 || o.variant > 5) return FASTSV_ERR_INVALID_ARG;
+    if (o.sparse_div < 0 || o.batch_sparse_div < 0) return FASTSV_ERR_INVALID_ARG;
     if (o.mode == FASTSV_MODE_ASYNC && o.variant >= 1 && o.variant <= 4) return FASTSV_ERR_INVALID_ARG;
     fastsv_ctx* h = new fastsv_ctx();
     h->opt = o;
@@ -960,6 +962,9 @@ fastsv_status fastsv_cc_batched(fastsv_t h, int32_t G, const int64_t* vtx_off, c
     prm.p = h->d_p;
     prm.gf = h->d_gf;
     prm.mngf = h->d_mngf;
+    prm.frontier = h->d_frontier;
+    prm.frontier_cap = N;
+    prm.sparse_div = h->opt.batch_sparse_div > 0 ? h->opt.batch_sparse_div : 0;
     prm.k2_tile = (int32_t)tile;
     prm.max_iters = h->opt.max_iters;
     prm.loop_limit = h->opt.max_iters + 1;

@@ -116,8 +116,8 @@ struct SingleParams {
     int32_t* p;
     int32_t* gf;
     int32_t* mngf;
-    int32_t* frontier;
-    int64_t sparse_max_deg;  // < 0: sparse iterations off
+    int32_t* frontier;       // room for n (segment, vertex) pairs
+    int32_t sparse_div;      // 0: sparse iterations off
     int64_t n, m;
     int32_t k2_tile;
     int32_t max_iters;
@@ -146,8 +146,9 @@ __global__ void k_setup_single(Ctx* ctx, SingleParams prm, WsPtrs ws) {
     s.changed = 0;
     s.user = 0;
     s.leader = 0;
-    s.pad = 0;
+    s.mode = 0;
     s.mngf = prm.mngf;
+    s.fr_deg = 0;
     ws.segs[0] = s;
     ctx->num_segs = 1;
     ctx->k2_tile = prm.k2_tile;
@@ -159,13 +160,14 @@ __global__ void k_setup_single(Ctx* ctx, SingleParams prm, WsPtrs ws) {
     ctx->k3_done = 0;
     ctx->any_active = s.active;
     ctx->val_status = 0;
-    ctx->sparse_enabled = prm.sparse_max_deg >= 0;
-    ctx->mode = 0;
+    ctx->sparse_enabled = prm.sparse_div > 0;
+    ctx->mode = MODE_DENSE;
     ctx->frontier = prm.frontier;
     ctx->frontier_len = 0;
     ctx->frontier_next = 0;
-    ctx->frontier_deg = 0;
-    ctx->sparse_max_deg = prm.sparse_max_deg;
+    ctx->frontier_cap = (unsigned int)(prm.n < 0x7fffffff ? prm.n : 0x7fffffff);
+    ctx->frontier_overflow = 0;
+    ctx->sparse_div = prm.sparse_div;
     ctx->sparse_iters = 0;
     for (int i = 0; i < TRACE_LEN; ++i) ctx->sum.trace[i] = 0;
 }
@@ -180,6 +182,9 @@ struct BatchParams {
     int32_t* p;
     int32_t* gf;
     int32_t* mngf;
+    int32_t* frontier;       // room for frontier_cap (segment, vertex) pairs
+    int64_t frontier_cap;
+    int32_t sparse_div;      // 0: sparse iterations off
     int32_t k2_tile;
     int32_t max_iters;
     int32_t loop_limit;
@@ -212,8 +217,9 @@ __global__ void k_setup_batched(Ctx* ctx, BatchParams prm, WsPtrs ws) {
         s.changed = 0;
         s.user = (int32_t)g;
         s.leader = (int32_t)g;
-        s.pad = 0;
+        s.mode = 0;
         s.mngf = prm.mngf + v0;
+        s.fr_deg = 0;
         ws.segs[g] = s;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -225,8 +231,14 @@ __global__ void k_setup_batched(Ctx* ctx, BatchParams prm, WsPtrs ws) {
         ctx->loop_iter = 0;
         ctx->k3_done = 0;
         ctx->val_status = 0;
-        ctx->sparse_enabled = 0;
-        ctx->mode = 0;
+        ctx->sparse_enabled = prm.sparse_div > 0;
+        ctx->mode = MODE_DENSE;
+        ctx->frontier = prm.frontier;
+        ctx->frontier_len = 0;
+        ctx->frontier_next = 0;
+        ctx->frontier_cap = (unsigned int)(prm.frontier_cap < 0x7fffffff ? prm.frontier_cap : 0x7fffffff);
+        ctx->frontier_overflow = 0;
+        ctx->sparse_div = prm.sparse_div;
         ctx->sparse_iters = 0;
         for (int i = 0; i < TRACE_LEN; ++i) ctx->sum.trace[i] = 0;
     }
@@ -938,14 +950,14 @@ constexpr int k2_smem_bytes() {
 // first kernel of every iteration: resets the loop condition to "stop" (only
 // the last CTA of k3_grandparent sets it back to "continue" when work
 // remains, so a device loop can never outlive its bookkeeping), and before a
-// full SpMV sets mngf to INF for every active graph
+// full SpMV sets mngf to INF for every active graph that runs one
 __global__ void k_iter_begin(Ctx* __restrict__ ctx, cudaGraphConditionalHandle cond, int use_cond) {
     if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
-    if (ctx->mode != 0) return;
+    if (!(ctx->mode & MODE_DENSE)) return;
     const int64_t total = ctx->k3_total;
     for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
         const Seg& S = ctx->segs[ctx->k3_tile_seg[t]];
-        if (!S.active) continue;
+        if (!S.active || S.mode != 0) continue;  // a pushing graph keeps its mngf
         const int64_t v0 = (t - S.k3_tile0) * K3_TILE;
         const int64_t v1 = min(v0 + K3_TILE, S.n);
         for (int64_t v = v0 + threadIdx.x; v < v1; v += blockDim.x) S.mngf[v] = INF;
@@ -965,7 +977,7 @@ __global__ void k_iter_begin(Ctx* __restrict__ ctx, cudaGraphConditionalHandle c
 template <typename RP, int THREADS, int ITEMS>
 __global__ void __launch_bounds__(THREADS) k2_spmv(Ctx* __restrict__ ctx, int block) {
     constexpr int TILE = THREADS * ITEMS;
-    if (ctx->mode != 0) return;
+    if (!(ctx->mode & MODE_DENSE)) return;
     extern __shared__ int32_t smem[];
     int32_t* s_rowend = smem;                 // local end offset of each row in the tile
     int32_t* s_mngf = smem + (TILE + 1);      // per-row minimum over the tile's entries
@@ -984,7 +996,7 @@ __global__ void __launch_bounds__(THREADS) k2_spmv(Ctx* __restrict__ ctx, int bl
 
     for (int64_t t = t_begin + blockIdx.x; t < T; t += gridDim.x) {
         const Seg* S = segs + tile_seg[t];
-        if (!segs[S->leader].active) continue;
+        if (!segs[S->leader].active || segs[S->leader].mode != 0) continue;
         const RP* __restrict__ rp = (const RP*)S->rp;
         const int32_t* __restrict__ gf = S->gf;
         int32_t* mngf = S->mngf;
@@ -1098,22 +1110,26 @@ __global__ void __launch_bounds__(THREADS) k2_spmv(Ctx* __restrict__ ctx, int bl
 // a1, sparse iteration (Section 4.2's SpMSpV): only vertices whose gf
 // changed in the last iteration can lower a neighbour's minimum, and gf never
 // increases, so min(old mngf, pushes of the new gf of changed vertices) is
-// exactly the SpMV of the new gf.  One warp per changed vertex.
+// exactly the SpMV of the new gf.  One warp per changed vertex; each graph
+// decides for itself, after every iteration, whether it pushes or runs a
+// full SpMV, and the frontier holds (graph, vertex) pairs of all of them.
 template <typename RP>
 __global__ void __launch_bounds__(256) k2_push(Ctx* __restrict__ ctx) {
-    if (ctx->mode != 1) return;
-    const Seg S = ctx->segs[0];
-    if (!S.active) return;
-    if (blockIdx.x == 0 && threadIdx.x == 0) ctx->sparse_iters++;
-    const RP* rp = (const RP*)S.rp;
+    if (!(ctx->mode & MODE_PUSH)) return;
+    const Seg* __restrict__ segs = ctx->segs;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && segs[0].active && segs[0].mode == 1) ctx->sparse_iters++;
     const int32_t* __restrict__ F = ctx->frontier;
     const unsigned len = ctx->frontier_len;
+    const int nsegs = ctx->num_segs;
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t i = warp; i < len; i += nwarps) {
-        const int32_t v = F[i];
-        if ((uint32_t)v >= (uint64_t)S.n) continue;
+        const int32_t sg = F[2 * i], v = F[2 * i + 1];
+        if ((uint32_t)sg >= (uint32_t)nsegs) continue;
+        const Seg& S = segs[sg];
+        if (!S.active || S.mode != 1 || (uint32_t)v >= (uint64_t)S.n) continue;
+        const RP* rp = (const RP*)S.rp;
         const int32_t g = S.gf[v];
         int64_t b = rp_at(rp, v), e = rp_at(rp, v + 1);
         if (b < 0) b = 0;
@@ -1174,11 +1190,15 @@ __device__ __forceinline__ void close_iteration(Ctx* ctx, cudaGraphConditionalHa
     const int tid = threadIdx.x;
     const int G = ctx->num_segs;
     const int max_iters = ctx->max_iters;
-    int any = 0;
+    const bool sparse = ctx->sparse_enabled && !ctx->frontier_overflow;
+    const int div = ctx->sparse_div > 0 ? ctx->sparse_div : 1;
+    int any = 0, dense = 0, push = 0;
     for (int s = tid; s < G; s += blockDim.x) {
         Seg* S = ctx->segs + s;
         if (!S->active || S->leader != s) continue;  // column blocks follow their graph
         unsigned int ch = atomicExch(&S->changed, 0u);
+        const unsigned long long deg = S->fr_deg;
+        S->fr_deg = 0;
         int it = S->iters + 1;
         S->iters = it;
         if (s == 0 && it <= TRACE_LEN) ctx->sum.trace[it - 1] = ch;
@@ -1190,24 +1210,27 @@ __device__ __forceinline__ void close_iteration(Ctx* ctx, cudaGraphConditionalHa
             S->status |= DEV_ERR_MAX_ITERS;
         } else {
             any = 1;
+            // next iteration: push from the vertices whose gf just changed
+            // when their rows are few enough, else a full SpMV
+            S->mode = (sparse && deg <= (unsigned long long)(S->m / div)) ? 1 : 0;
+            if (S->mode)
+                push = 1;
+            else
+                dense = 1;
         }
     }
     any = __syncthreads_or(any);
+    dense = __syncthreads_or(dense);
+    push = __syncthreads_or(push);
     if (tid == 0) {
         ctx->k3_done = 0;
         int li = ctx->loop_iter + 1;
         ctx->loop_iter = li;
         ctx->any_active = any;
-        if (ctx->sparse_enabled) {
-            // next iteration: push from the vertices whose gf just changed
-            // when their rows are few enough, else a full SpMV
-            const unsigned len = ctx->frontier_next;
-            const unsigned long long deg = ctx->frontier_deg;
-            ctx->frontier_len = len;
-            ctx->frontier_next = 0;
-            ctx->frontier_deg = 0;
-            ctx->mode = (deg <= (unsigned long long)ctx->sparse_max_deg) ? 1 : 0;
-        }
+        ctx->frontier_len = ctx->frontier_next;
+        ctx->frontier_next = 0;
+        ctx->frontier_overflow = 0;
+        ctx->mode = (dense ? MODE_DENSE : 0) | (push ? MODE_PUSH : 0);
         if (use_cond) cudaGraphSetConditional(cond, (any && li < ctx->loop_limit) ? 1u : 0u);
     }
 }
@@ -1268,13 +1291,22 @@ __global__ void __launch_bounds__(K3_THREADS)
                 total += x;
             }
             if (total) atomicAdd(&S->changed, (unsigned int)total);
-            s_base = (track && total) ? atomicAdd(&ctx->frontier_next, (unsigned)total) : 0u;
+            s_base = 0xffffffffu;  // no room: the frontier is dropped for one iteration
+            if (track && total) {
+                const unsigned b = atomicAdd(&ctx->frontier_next, (unsigned)total);
+                if ((unsigned long long)b + total <= ctx->frontier_cap)
+                    s_base = b;
+                else
+                    ctx->frontier_overflow = 1;
+            }
         }
         __syncthreads();
         if (track && c) {
-            // frontier of the next iteration: the changed vertices of this
-            // tile, and the sum of their degrees
+            // frontier of the next iteration: the (graph, vertex) pairs of
+            // this tile's changed vertices, and the sum of their degrees
+            const int32_t sg = ctx->k3_tile_seg[t];
             const RP* rp = (const RP*)S->rp;
+            const bool room = s_base != 0xffffffffu;
             unsigned off = s_base + (unsigned)s_woff[tid >> 5];
             unsigned long long dsum = 0;
 #pragma unroll
@@ -1282,14 +1314,18 @@ __global__ void __launch_bounds__(K3_THREADS)
                 const unsigned mask = masks[q];
                 if (mask >> lane & 1u) {
                     const int64_t v = v0 + tid + q * K3_THREADS;
-                    ctx->frontier[off + __popc(mask & ((1u << lane) - 1u))] = (int32_t)v;
+                    if (room) {
+                        const int64_t at = 2 * (int64_t)(off + __popc(mask & ((1u << lane) - 1u)));
+                        ctx->frontier[at] = sg;
+                        ctx->frontier[at + 1] = (int32_t)v;
+                    }
                     dsum += (unsigned long long)(rp_at(rp, v + 1) - rp_at(rp, v));
                 }
                 off += (unsigned)__popc(mask);
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) dsum += __shfl_down_sync(0xffffffffu, dsum, o);
-            if (lane == 0 && dsum) atomicAdd(&ctx->frontier_deg, dsum);
+            if (lane == 0 && dsum) atomicAdd(&S->fr_deg, dsum);
         }
         __syncthreads();
     }

@@ -36,9 +36,14 @@ struct Seg {
     int32_t user;        // owner tag (pool slot id), unused by the kernels
     int32_t leader;      // segment whose state governs this one: itself, or for a
                          // column block of a graph, the graph's own segment
-    int32_t pad;
+    int32_t mode;        // this iteration: 0 = full SpMV, 1 = push from the frontier
     int32_t* mngf;       // per-row minimum of gf over neighbours, kept across iterations
+    unsigned long long fr_deg;  // degree sum of this iteration's changed vertices (being filled)
 };
+
+// Ctx::mode bits: some active graph runs a full SpMV / pushes this iteration
+constexpr int32_t MODE_DENSE = 1;
+constexpr int32_t MODE_PUSH = 2;
 
 struct Summary {
     int64_t iterations;     // max over segments
@@ -66,17 +71,18 @@ struct Ctx {
     unsigned int k3_done;    // CTA ticket for the last-block epilogue
     int32_t any_active;
     int32_t val_status;      // validation result bits
-    // sparse iterations (single graph): vertices whose gf changed in the last
-    // iteration push their new gf to their neighbours' mngf instead of a full SpMV
+    // sparse iterations: a graph whose changed vertices have a degree sum of at
+    // most m / sparse_div pushes their new gf to the neighbours' mngf instead
+    // of running a full SpMV (decided per graph after every iteration)
     int32_t sparse_enabled;
-    int32_t mode;                  // this iteration: 0 = full SpMV, 1 = push from the frontier
-    int32_t* frontier;             // vertices whose gf changed in the last iteration
-    unsigned int frontier_len;
+    int32_t mode;                  // MODE_DENSE | MODE_PUSH: the kinds of work this iteration has
+    int32_t* frontier;             // (segment, vertex) pairs whose gf changed in the last iteration
+    unsigned int frontier_len;     // pairs in the frontier
     unsigned int frontier_next;    // being filled by this iteration's k3
-    unsigned long long frontier_deg;   // sum of their degrees (being filled)
-    int64_t sparse_max_deg;        // push when the frontier's degree sum is at most this
-    int32_t sparse_iters;          // iterations run in push mode in this call
-    int32_t pad2;
+    unsigned int frontier_cap;     // pairs the buffer holds
+    int32_t frontier_overflow;     // this iteration's changes did not fit: no pushes next
+    int32_t sparse_div;
+    int32_t sparse_iters;          // iterations graph 0 ran in push mode in this call
     Summary sum;
 };
 

@@ -9,6 +9,7 @@
 // slot's state (f, p, gf, iteration count) stays resident between steps, so
 // graphs admitted later join the running batch at an iteration boundary and
 // every graph follows exactly the iteration sequence it has alone.
+#include <algorithm>
 #include <cstring>
 #include <map>
 #include <vector>
@@ -67,8 +68,9 @@ __global__ void k_pool_admit(Ctx* ctx, Seg* segs, int32_t* k2_seg, int32_t* k2_r
         s.changed = 0;
         s.user = a.slot;
         s.leader = a.slot;
-        s.pad = 0;
+        s.mode = 0;  // a restored graph's mngf is not kept: its first step runs a full SpMV
         s.mngf = a.mngf;
+        s.fr_deg = 0;
         segs[a.slot] = s;
     }
     if (i == 0) {
@@ -83,16 +85,39 @@ __global__ void k_pool_admit(Ctx* ctx, Seg* segs, int32_t* k2_seg, int32_t* k2_r
         ctx->loop_iter = 0;
         ctx->k3_done = 0;
         ctx->val_status = 0;
-        ctx->sparse_enabled = 0;
-        ctx->mode = 0;
     }
 }
 
-// start of a step: the device loop's iteration counter and cap
-__global__ void k_pool_begin(Ctx* ctx, int32_t loop_limit) {
-    ctx->loop_iter = 0;
-    ctx->loop_limit = loop_limit;
-    ctx->k3_done = 0;
+// start of a step: the device loop's iteration counter and cap, and the
+// sparse-iteration state (pool-owned frontier; kinds of work of the first
+// iteration from the resident graphs' modes)
+__global__ void k_pool_begin(Ctx* ctx, int32_t loop_limit, int32_t* frontier, int64_t frontier_cap,
+                             int32_t sparse_div) {
+    __shared__ int s_dense, s_push;
+    if (threadIdx.x == 0) s_dense = s_push = 0;
+    __syncthreads();
+    int dense = 0, push = 0;
+    for (int i = threadIdx.x; i < ctx->num_segs; i += blockDim.x) {
+        const Seg& S = ctx->segs[i];
+        if (!S.active) continue;
+        if (S.mode)
+            push = 1;
+        else
+            dense = 1;
+    }
+    if (dense) s_dense = 1;
+    if (push) s_push = 1;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ctx->loop_iter = 0;
+        ctx->loop_limit = loop_limit;
+        ctx->k3_done = 0;
+        ctx->sparse_enabled = sparse_div > 0 && frontier != nullptr;
+        ctx->sparse_div = sparse_div;
+        ctx->frontier = frontier;
+        ctx->frontier_cap = (unsigned int)(frontier_cap < 0x7fffffff ? frontier_cap : 0x7fffffff);
+        ctx->mode = (s_dense ? MODE_DENSE : 0) | (s_push ? MODE_PUSH : 0);
+    }
 }
 
 struct Slot {
@@ -124,6 +149,8 @@ struct Pool {
     int32_t* d_k2_seg = nullptr;
     int32_t* d_k2_row = nullptr;
     int32_t* d_k3_seg = nullptr;
+    int32_t* d_frontier = nullptr;  // (slot, vertex) pairs of the last iteration's changed vertices
+    int64_t frontier_cap = 0;       // pairs
     char* arena = nullptr;
     size_t budget = 0, used = 0;
     std::map<size_t, size_t> free_list;  // offset -> size, coalesced
@@ -194,6 +221,7 @@ void pool_release(fastsv_ctx* h) {
     if (P->d_k2_seg) cudaFree(P->d_k2_seg);
     if (P->d_k2_row) cudaFree(P->d_k2_row);
     if (P->d_k3_seg) cudaFree(P->d_k3_seg);
+    if (P->d_frontier) cudaFree(P->d_frontier);
     if (P->arena) cudaFree(P->arena);
     if (P->copy_stream) cudaStreamDestroy(P->copy_stream);
     if (P->out_stream) cudaStreamDestroy(P->out_stream);
@@ -230,6 +258,10 @@ fastsv_status fastsv_pool_create(fastsv_t h, size_t budget, int32_t max_slots) {
     // every slot needs at least 4(n+m) bytes, so n + m <= budget / 4 over all slots
     const int64_t cap2 = (int64_t)(P->budget / 4) / tile + max_slots + 1;
     const int64_t cap3 = (int64_t)(P->budget / 16) / K3_TILE + max_slots + 1;
+    // every resident vertex needs >= 20 bytes of the arena; a larger frontier
+    // than 2^27 pairs (1 GiB) overflows into a full SpMV for one iteration
+    const int64_t fcap = std::min<int64_t>((int64_t)(P->budget / 20) + 1, (int64_t)1 << 27);
+    P->frontier_cap = fcap;
     fastsv_status st = FASTSV_OK;
     cudaError_t e = cudaSuccess;
     if ((st = dev_alloc(h, (void**)&P->d_ctx, sizeof(Ctx))) != FASTSV_OK ||
@@ -237,6 +269,7 @@ fastsv_status fastsv_pool_create(fastsv_t h, size_t budget, int32_t max_slots) {
         (st = dev_alloc(h, (void**)&P->d_k2_seg, 4 * (size_t)cap2)) != FASTSV_OK ||
         (st = dev_alloc(h, (void**)&P->d_k2_row, 4 * (size_t)cap2)) != FASTSV_OK ||
         (st = dev_alloc(h, (void**)&P->d_k3_seg, 4 * (size_t)cap3)) != FASTSV_OK ||
+        (st = dev_alloc(h, (void**)&P->d_frontier, 8 * (size_t)fcap)) != FASTSV_OK ||
         (st = dev_alloc(h, (void**)&P->arena, P->budget)) != FASTSV_OK) {
         pool_release(h);
         return st;
@@ -467,7 +500,8 @@ fastsv_status fastsv_pool_step(fastsv_t h, int32_t iters, void* stream) {
         h->loop_limit_host = iters;
         const bool graph = h->opt.use_graph != 0;
         // every step runs up to `iters` iterations, whether or not it admitted
-        k_pool_begin<<<1, 1, 0, s>>>(P->d_ctx, iters);
+        k_pool_begin<<<1, 256, 0, s>>>(P->d_ctx, iters, P->d_frontier, P->frontier_cap,
+                                       h->opt.batch_sparse_div > 0 ? h->opt.batch_sparse_div : 0);
         h->launches += 1;
         FSV_CUDA(h, cudaGetLastError());
         fastsv_status st = run_loop(h, P->d_ctx, 0, 0, items, 0, s);

@@ -45,14 +45,15 @@ def test_host_only_entry_points():
     # invalid handles are rejected on the host without touching a device
     assert fsv._lib.load().fastsv_destroy(None) == fsv.FASTSV_ERR_INVALID_ARG
     assert fsv._lib.load().fastsv_cc(None, 5, None, None, None, None) == fsv.FASTSV_ERR_INVALID_ARG
-    assert o.variant == 0 and o.sparse_div == 2 and o.k2_threads == 256
+    assert o.variant == 0 and o.sparse_div == 2 and o.k2_threads == 256 and o.batch_sparse_div == 0
 
 
 def test_option_validation_is_host_only():
     """Bad options are refused by fastsv_create before any CUDA call."""
     import paper_1910_05971_gb300 as fsv
     lib = fsv._lib.load()
-    for field, value in (("variant", 6), ("variant", -1), ("mode", 2), ("rowptr_bits", 16), ("max_iters", 0)):
+    for field, value in (("variant", 6), ("variant", -1), ("mode", 2), ("rowptr_bits", 16), ("max_iters", 0),
+                         ("sparse_div", -1), ("batch_sparse_div", -3)):
         o = fsv.fastsv_default_options()
         setattr(o, field, value)
         h = C.c_void_p()

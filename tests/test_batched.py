@@ -85,3 +85,26 @@ def test_batched_config_full():
     assert np.array_equal(lab, ref_lab)
     assert np.array_equal(iters, ref_it)
     assert launches == 5 + 5 * int(ref_it.max())
+
+
+@pytest.mark.parametrize("sparse_div", [0, 1, 2, 1 << 20])
+def test_batch_per_graph_sparse_iterations_are_exact(sparse_div):
+    """Each graph of a batch decides after every iteration whether it pushes
+    from its changed vertices or runs a full SpMV (Section 4.2); pushing is
+    exact, so labels and iteration counts match the oracle whatever the
+    threshold (push when the changed vertices' degree sum is at most
+    m / sparse_div: 0 never pushes, 1 pushes after every first iteration,
+    2^20 practically never)."""
+    graphs = [graphgen.rmat(12, 16, seed=31, permute=True), graphgen.grid(60, 0.55, 40, seed=5),
+              oracle.csr_from_edges(2000, [(i, i + 1) for i in range(1999)]),
+              oracle.csr_from_edges(0, []), oracle.csr_from_edges(1, [])]
+    graphs += [graphgen.rmat(9, 8, seed=40 + k) for k in range(20)]
+    batch = graphgen.Batch.from_graphs(graphs)
+    lab, iters, st, _ = _run_batch(batch, batch_sparse_div=sparse_div)
+    ref_lab, ref_it = oracle_batch(batch)
+    assert np.array_equal(lab, ref_lab)
+    assert np.array_equal(iters, ref_it)
+    if sparse_div == 1:
+        assert st["sparse_iters"] > 0  # graph 0 pushed in at least one iteration
+    if sparse_div == 0:
+        assert st["sparse_iters"] == 0

@@ -231,3 +231,36 @@ def test_evict_and_restore_errors():
     f, it, _, _ = oracle.fastsv(rp, ci)
     assert np.array_equal(lab, f) and done[0] == it
     pool.close()
+
+
+@pytest.mark.parametrize("sparse_div", [0, 1])
+def test_pool_sparse_iterations_match_alone(sparse_div):
+    """Resident graphs choose push or full SpMV per iteration on their own;
+    with pushes forced (1) or off (0) every graph still gets its own labels
+    and iteration count."""
+    from paper_1910_05971_gb300.serve import PoolBackend
+    graphs = _graphs(24, seed=7)
+    ref = _alone(graphs)
+    pool = PoolBackend(64 << 20, 16, batch_sparse_div=sparse_div)
+    labels = [np.empty(max(len(rp) - 1, 1), np.int32) for rp, _ in graphs]
+    pending = list(range(len(graphs)))
+    slot_of, done = {}, {}
+    steps = 0
+    while len(done) < len(graphs):
+        for _ in range(4):
+            if not pending:
+                break
+            slot = pool.add(graphs[pending[0]][0], graphs[pending[0]][1], labels[pending[0]])
+            if slot is None:
+                break
+            slot_of[slot] = pending.pop(0)
+        pool.step(1)
+        steps += 1
+        for slot, iters in pool.poll()[0]:
+            done[slot_of.pop(slot)] = iters
+        assert steps < 10000
+    for g, (f, it) in enumerate(ref):
+        n = len(graphs[g][0]) - 1
+        assert np.array_equal(labels[g][:n], f), g
+        assert done[g] == it, (g, done[g], it)
+    pool.close()
