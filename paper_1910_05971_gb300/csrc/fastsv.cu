@@ -514,7 +514,7 @@ static fastsv_status finish_call(fastsv_ctx* h, cudaStream_t s, int32_t* iters_o
     return FASTSV_OK;
 }
 
-// validation needs its verdict before any hooking kernel reads the graph
+// validation needs its result before any hooking kernel reads the graph
 static fastsv_status run_validation(fastsv_ctx* h, int rp64, cudaStream_t s) {
     if (!h->opt.validate) return FASTSV_OK;
     if (rp64)
@@ -577,7 +577,7 @@ static fastsv_status launch_block_build(fastsv_ctx* h, int nb, int shift, int64_
     int32_t* start = h->d_rpB;  // run starts of every (row, block)
     FSV_CUDA(h, cudaMemsetAsync(descents, 0, sizeof(long long), s));
     k_sorted_check<RP><<<g, 256, 0, s>>>(ctx, descents);
-    k_sorted_verdict<<<1, 1, 0, s>>>(descents, flag);
+    k_sorted_result<<<1, 1, 0, s>>>(descents, flag);
     // sorted rows: run starts by binary search, counts as their differences
     k_block_runs<RP><<<g, 256, 0, s>>>(ctx, start, h->d_counts, nb, shift, flag);
     {

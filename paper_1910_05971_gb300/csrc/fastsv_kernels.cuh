@@ -604,7 +604,7 @@ __global__ void k_sorted_check(const Ctx* ctx, long long* descents) {
     if ((threadIdx.x & 31) == 0 && d) atomicAdd((unsigned long long*)descents, (unsigned long long)d);
 }
 
-__global__ void k_sorted_verdict(const long long* descents, int32_t* unsorted) { *unsorted = *descents != 0; }
+__global__ void k_sorted_result(const long long* descents, int32_t* unsorted) { *unsorted = *descents != 0; }
 
 // Sorted rows: start[k][u] = first position of row u whose column block is
 // >= k (the row end if none), found by binary search per (row, block)
@@ -1014,6 +1014,9 @@ __global__ void __launch_bounds__(THREADS) k2_spmv(Ctx* __restrict__ ctx, int bl
         const int D = (int)(d1 - d0);
         const RP* __restrict__ rpt = rp + x0 + 1;     // row ends of the tile's rows
         const int32_t* __restrict__ cit = S->ci + y0; // the tile's entries
+        // first iteration of the graph: gf is still the identity (every
+        // vertex its own root), so gf[v] = v and the gather is skipped
+        const bool ident = segs[S->leader].iters == 0;
 
         // phase 1: row ends, and the gathered grandparents of the tile's entries
         for (int i = tid; i < R; i += THREADS) {
@@ -1032,7 +1035,7 @@ __global__ void __launch_bounds__(THREADS) k2_spmv(Ctx* __restrict__ ctx, int bl
 #pragma unroll
             for (int q = 0; q < ITEMS; ++q) {
                 const int j = tid + q * THREADS;
-                if (j < E) s_val[j] = ((uint32_t)c[q] < (uint64_t)n) ? __ldg(gf + c[q]) : INF;
+                if (j < E) s_val[j] = ((uint32_t)c[q] < (uint64_t)n) ? (ident ? c[q] : __ldg(gf + c[q])) : INF;
             }
         }
         __syncthreads();
