@@ -654,6 +654,34 @@ static fastsv_status ensure_block_workspace(fastsv_ctx* h, int nb, int64_t n, in
     return FASTSV_OK;
 }
 
+// one iteration on segment 0's own tiles (BUILD_TILE items each), launched
+// kernel by kernel: the first iteration of a column-blocked solve.  Its SpMV
+// gathers nothing, so the per-tile merge-path search is most of its work: the
+// 64 x 16 instance spends one search on 16 items.
+static_assert(BUILD_TILE == 64 * 16, "first unblocked iteration runs the 64 x 16 SpMV instance");
+static fastsv_status first_iteration_unblocked(fastsv_ctx* h, int rp64, cudaStream_t s) {
+    IterKernels K;
+    fastsv_status st = iter_kernels(h, rp64, rp64, 8, &K);
+    if (st != FASTSV_OK) return st;
+    const void* spmv = k2_func(rp64, 16, 64);
+    const int smem = k2_smem(16, 64);
+    int grid = 0;
+    if ((st = k2_grid_for(h, rp64, 16, 64, &grid)) != FASTSV_OK) return st;
+    Ctx* ctx = h->d_ctx;
+    cudaGraphConditionalHandle none = 0;
+    int no_cond = 0, blk = -1;
+    void* a_begin[] = {(void*)&ctx, (void*)&none, (void*)&no_cond};
+    void* a_spmv[] = {(void*)&ctx, (void*)&blk};
+    void* a_ctx[] = {(void*)&ctx};
+    void* a_k3[] = {(void*)&ctx, (void*)&none, (void*)&no_cond};
+    FSV_CUDA(h, cudaLaunchKernel((const void*)k_iter_begin, dim3(K.vtx_grid), dim3(256), a_begin, 0, s));
+    FSV_CUDA(h, cudaLaunchKernel(spmv, dim3(grid), dim3(64), a_spmv, smem, s));
+    FSV_CUDA(h, cudaLaunchKernel(K.hook, dim3(K.vtx_grid), dim3(K3_THREADS), a_ctx, 0, s));
+    FSV_CUDA(h, cudaLaunchKernel(K.k3, dim3(K.vtx_grid), dim3(K3_THREADS), a_k3, 0, s));
+    h->pending_fixed_launches += 4;
+    return FASTSV_OK;
+}
+
 static fastsv_status solve_single(fastsv_ctx* h, int64_t n, int64_t m, const void* rp, const int32_t* ci,
                                   int32_t* labels, cudaStream_t s) {
     const int rp64 = h->opt.rowptr_bits == 64;
@@ -707,6 +735,13 @@ static fastsv_status solve_single(fastsv_ctx* h, int64_t n, int64_t m, const voi
     if ((st = run_validation(h, rp64, s)) != FASTSV_OK) return st;
     int loop_rp64 = rp64;
     if (nb_eff > 1) {
+        // The graph's first iteration needs no gathers (gf is still the
+        // identity), so it gains nothing from column blocks: it runs on the
+        // original CSR, over the build's tiles (BUILD_TILE items), before the
+        // block copy.
+        k_init_state<<<setup_grid(h), 256, 0, s>>>(h->d_ctx);
+        h->pending_fixed_launches += 1;
+        if ((st = first_iteration_unblocked(h, rp64, s)) != FASTSV_OK) return st;
         // split the columns into blocks, then partition every block's CSR
         st = rp64 ? launch_block_build<int64_t>(h, nb_eff, shift, n, s)
                   : launch_block_build<int32_t>(h, nb_eff, shift, n, s);
@@ -716,9 +751,10 @@ static fastsv_status solve_single(fastsv_ctx* h, int64_t n, int64_t m, const voi
         k_partition<int32_t><<<setup_grid(h), 256, 0, s>>>(h->d_ctx);
         h->pending_fixed_launches += 3;
         loop_rp64 = 0;
+    } else {
+        k_init_state<<<setup_grid(h), 256, 0, s>>>(h->d_ctx);
+        h->pending_fixed_launches += 1;
     }
-    k_init_state<<<setup_grid(h), 256, 0, s>>>(h->d_ctx);
-    h->pending_fixed_launches += 1;
     if (variant == 1) {
         kv_iota<<<setup_grid(h), 256, 0, s>>>(h->d_gf, n);  // grandparents for the root test
         h->pending_fixed_launches += 1;

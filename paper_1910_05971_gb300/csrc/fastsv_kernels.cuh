@@ -936,6 +936,7 @@ __global__ void k_setup_blocks(Ctx* ctx, const int32_t* rpB, const int32_t* colB
     segs[0].k2_ntiles = 0;
     ctx->num_segs = nb + 1;
     ctx->k2_tile = k2_tile;
+    ctx->loop_iter = 0;  // an iteration run before the blocks is not the device loop's
 }
 
 // ---------------------------------------------------------------------------
