@@ -592,9 +592,22 @@ __global__ void k_sorted_check(const Ctx* ctx, long long* descents) {
     const uint32_t* ci = (const uint32_t*)S.ci;
     const int64_t n = S.n, m = S.m;
     long long d = 0;
+    const int64_t tid0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e + 1 < m; e += stride)
-        d += ci[e] > ci[e + 1];
+    // adjacent pairs (e, e+1): four entries per 16-byte load when col_idx is
+    // 16-byte aligned, the pair across each group from the next entry
+    int64_t e_tail = 0;
+    if ((reinterpret_cast<uintptr_t>(ci) & 15) == 0) {
+        const int64_t groups = m / 4;
+        const uint4* ci4 = reinterpret_cast<const uint4*>(ci);
+        for (int64_t g = tid0; g < groups; g += stride) {
+            const uint4 v = __ldcs(ci4 + g);
+            d += (v.x > v.y) + (v.y > v.z) + (v.z > v.w);
+            if (4 * g + 4 < m) d += v.w > __ldg(ci + 4 * g + 4);
+        }
+        e_tail = groups * 4;
+    }
+    for (int64_t e = e_tail + tid0; e + 1 < m; e += stride) d += ci[e] > ci[e + 1];
     for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x + 1; u < n; u += stride) {
         const int64_t b = rp_at(rp, u);
         if (b > 0 && b < m && b < rp_at(rp, u + 1)) d -= ci[b - 1] > ci[b];
