@@ -122,15 +122,21 @@ typedef struct {
     int32_t converged;         /* 1 if every graph reached an unchanged f[f] */
     float ms_total;            /* device time of the last call's work on its stream (timing = 1) */
     float ms_setup;            /* of which: partitioning, state initialisation, validation */
-    float ms_k2;               /* host-loop mode only: total time of the full-SpMV kernel */
-    float ms_k3;               /* host-loop mode only: total time of the grandparent kernel */
+    float ms_k2;               /* host-loop mode only: total time of the full-SpMV kernel over the
+                                  timed_dense_iters iterations that ran it */
+    float ms_k3;               /* host-loop mode only: total time of the grandparent kernel (timed_iters) */
     float ms_push;             /* host-loop mode only: total time of the sparse (push) iterations' SpMSpV */
-    float ms_hook;             /* host-loop mode only: total time of the hooking kernel */
+    float ms_hook;             /* host-loop mode only: total time of the hooking kernel (timed_iters) */
     int32_t sparse_iters;      /* single-graph calls: iterations that pushed from the changed vertices */
-    int32_t dense_iters;       /* iterations that ran the full SpMV */
+    int32_t dense_iters;       /* iterations that ran the full SpMV (iterations - sparse_iters) */
     int32_t trace_len;         /* entries valid in changed_per_iter */
     int32_t col_blocks;        /* column blocks the last single-graph call used (1 = unblocked) */
     int64_t changed_per_iter[64]; /* single-graph calls: grandparents changed in iteration i */
+    int32_t timed_iters;       /* host-loop mode: iterations the ms_k2 .. ms_hook fields cover.  A
+                                  column-blocked call runs its first iteration before the loop, on the
+                                  original CSR (no gathers are needed while gf is the identity); that
+                                  iteration is part of ms_setup */
+    int32_t timed_dense_iters; /* host-loop mode: of those, the iterations that ran the full SpMV */
 } fastsv_stats;
 
 /* Fill *opt with the defaults listed above. */

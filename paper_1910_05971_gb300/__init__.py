@@ -46,7 +46,8 @@ def stats_dict(s: fastsv_stats) -> dict:
     return dict(n=s.n, m=s.m, iterations=s.iterations, status=s.status, converged=bool(s.converged),
                 ms_total=s.ms_total, ms_setup=s.ms_setup, ms_k2=s.ms_k2, ms_k3=s.ms_k3, ms_push=s.ms_push,
                 ms_hook=s.ms_hook, sparse_iters=s.sparse_iters, dense_iters=s.dense_iters,
-                col_blocks=s.col_blocks, changed_per_iter=[int(s.changed_per_iter[i]) for i in range(s.trace_len)])
+                col_blocks=s.col_blocks, changed_per_iter=[int(s.changed_per_iter[i]) for i in range(s.trace_len)],
+                timed_iters=s.timed_iters, timed_dense_iters=s.timed_dense_iters)
 
 
 class FastSV:

@@ -72,6 +72,8 @@ class fastsv_stats(C.Structure):
         ("trace_len", C.c_int32),
         ("col_blocks", C.c_int32),
         ("changed_per_iter", C.c_int64 * 64),
+        ("timed_iters", C.c_int32),
+        ("timed_dense_iters", C.c_int32),
     ]
 
 

@@ -325,6 +325,7 @@ fastsv_status run_loop(fastsv_ctx* h, Ctx* ctx, int rp64_orig, int rp64_dense, i
     h->ms_hook = t_hook;
     h->ms_k3 = t_k3;
     h->dense_iters = dense;
+    h->timed_iters = iters;
     h->pending_loop_kernels = 0;
     return rc;
 }
@@ -394,6 +395,7 @@ static fastsv_status run_variant_loop(fastsv_ctx* h, Ctx* ctx, int rp64, int ite
     h->ms_k2 = t_spmv;
     h->ms_hook = t_rest;
     h->dense_iters = iters;
+    h->timed_iters = iters;
     h->pending_loop_kernels = 0;
     return rc;
 }
@@ -501,8 +503,11 @@ static void order_after_previous(fastsv_ctx* h, cudaStream_t s) {
 
 static fastsv_status finish_call(fastsv_ctx* h, cudaStream_t s, int32_t* iters_out, int64_t n, int64_t m,
                                  bool single) {
-    k_finish<<<1, 256, 0, s>>>(h->d_ctx, iters_out);
-    h->pending_fixed_launches += 1;
+    k_finish<<<1, 256, 0, s>>>(h->d_ctx, iters_out, h->pending_loop_kernels);
+    // launches made from the host count now; the device loop's count arrives
+    // with the summary
+    h->launches += h->pending_fixed_launches + 1;
+    h->pending_fixed_launches = 0;
     FSV_CUDA(h, cudaGetLastError());
     FSV_CUDA(h, cudaMemcpyAsync(h->h_sum, &h->d_ctx->sum, sizeof(Summary), cudaMemcpyDeviceToHost, s));
     FSV_CUDA(h, cudaEventRecord(h->ev_end, s));
@@ -708,6 +713,7 @@ static fastsv_status solve_single(fastsv_ctx* h, int64_t n, int64_t m, const voi
     h->pending_fixed_launches = 0;
     h->ms_k2 = h->ms_k3 = h->ms_push = h->ms_hook = 0.f;
     h->dense_iters = 0;
+    h->timed_iters = 0;
     h->last_col_blocks = nb_eff;
     FSV_CUDA(h, cudaEventRecord(h->ev_start, s));
     SingleParams prm;
@@ -987,6 +993,7 @@ fastsv_status fastsv_cc_batched(fastsv_t h, int32_t G, const int64_t* vtx_off, c
     h->pending_fixed_launches = 0;
     h->ms_k2 = h->ms_k3 = h->ms_push = h->ms_hook = 0.f;
     h->dense_iters = 0;
+    h->timed_iters = 0;
     FSV_CUDA(h, cudaEventRecord(h->ev_start, s));
     BatchParams prm;
     prm.G = G;
@@ -1036,8 +1043,7 @@ fastsv_status fastsv_get_stats(fastsv_t h, fastsv_stats* out) {
         }
         h->pending = false;
         const Summary& S = *h->h_sum;
-        h->launches += h->pending_fixed_launches + (int64_t)h->pending_loop_kernels * S.loop_iter;
-        h->pending_fixed_launches = 0;
+        h->launches_loop_dev = (int64_t)S.loop_kernels;
         int st = FASTSV_OK;
         if (S.status & (DEV_ERR_BAD_ROWPTR | DEV_ERR_BAD_COLIDX | DEV_ERR_ASYMMETRIC))
             st = FASTSV_ERR_INVALID_GRAPH;
@@ -1068,7 +1074,9 @@ fastsv_status fastsv_get_stats(fastsv_t h, fastsv_stats* out) {
     out->ms_push = h->ms_push;
     out->ms_hook = h->ms_hook;
     out->sparse_iters = S.sparse_iters;
-    out->dense_iters = h->opt.use_graph ? (int32_t)(S.iterations - S.sparse_iters) : h->dense_iters;
+    out->dense_iters = (int32_t)(S.iterations - S.sparse_iters);
+    out->timed_iters = h->opt.use_graph ? 0 : h->timed_iters;
+    out->timed_dense_iters = h->opt.use_graph ? 0 : h->dense_iters;
     int len = (int)(S.iterations < TRACE_LEN ? S.iterations : TRACE_LEN);
     out->trace_len = h->single ? len : 0;
     out->col_blocks = h->single ? h->last_col_blocks : 1;
@@ -1078,6 +1086,10 @@ fastsv_status fastsv_get_stats(fastsv_t h, fastsv_stats* out) {
 
 int32_t fastsv_last_cuda_error(fastsv_t h) { return h ? h->last_cuda_error : 0; }
 
-int64_t fastsv_kernel_launches(fastsv_t h) { return h ? h->launches : 0; }
+// the layouts the Python binding mirrors (its tests pin the same sizes)
+static_assert(sizeof(fastsv_options) == 64, "fastsv_options layout");
+static_assert(sizeof(fastsv_stats) == 592, "fastsv_stats layout");
+
+int64_t fastsv_kernel_launches(fastsv_t h) { return h ? h->launches + h->launches_loop_dev : 0; }
 
 }  // extern "C"

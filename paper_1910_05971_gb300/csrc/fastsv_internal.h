@@ -95,10 +95,12 @@ struct fastsv_ctx {
     bool pending = false;      // a call whose summary has not been read yet
     bool single = true;        // last call was a single-graph call
     float ms_k2 = 0.f, ms_k3 = 0.f, ms_push = 0.f, ms_hook = 0.f;
-    int32_t dense_iters = 0;
+    int32_t dense_iters = 0;   // host loop: timed iterations that ran the full SpMV
+    int32_t timed_iters = 0;   // host loop: iterations timed by ms_k2 .. ms_hook
     float ms_total_cache = 0.f, ms_setup_cache = 0.f;
     int64_t launches = 0;      // kernels launched, settled by fastsv_get_stats
     int64_t pending_fixed_launches = 0;  // set-up kernels of the pending call
+    int64_t launches_loop_dev = 0;       // device-loop kernels of every call up to the last synchronised one
     int pending_loop_kernels = 0;        // kernels per device-loop iteration of the pending call
     int alloc_count = 0;
     int32_t loop_limit_host = 0;         // iteration cap of the host-loop mode

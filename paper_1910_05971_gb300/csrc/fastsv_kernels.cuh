@@ -1360,7 +1360,9 @@ __global__ void __launch_bounds__(K3_THREADS)
 }
 
 // end of a call: per-graph iteration counts and the summary
-__global__ void k_finish(Ctx* ctx, int32_t* iters_out) {
+// per-call summary; also counts the call's device-loop kernels (loop_iter
+// iterations of loop_kernels each) into the context's running total
+__global__ void k_finish(Ctx* ctx, int32_t* iters_out, int loop_kernels) {
     __shared__ long long s_it[256];
     __shared__ int s_st[256], s_cv[256], s_act[256];
     const int G = ctx->num_segs;
@@ -1396,6 +1398,8 @@ __global__ void k_finish(Ctx* ctx, int32_t* iters_out) {
         ctx->sum.loop_iter = ctx->loop_iter;
         ctx->sum.num_active = s_act[0];
         ctx->sum.sparse_iters = ctx->sparse_iters;
+        ctx->loop_kernels_total += (unsigned long long)ctx->loop_iter * (unsigned long long)loop_kernels;
+        ctx->sum.loop_kernels = ctx->loop_kernels_total;
     }
 }
 

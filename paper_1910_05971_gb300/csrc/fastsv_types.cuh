@@ -53,6 +53,7 @@ struct Summary {
     int32_t num_active;     // segments still active
     int32_t sparse_iters;   // iterations that pushed from the frontier instead of a full SpMV
     int32_t pad;
+    unsigned long long loop_kernels;  // device-loop kernel launches of every call on this context so far
     unsigned long long trace[TRACE_LEN];  // segment 0: changed count per iteration
 };
 
@@ -83,6 +84,7 @@ struct Ctx {
     int32_t frontier_overflow;     // this iteration's changes did not fit: no pushes next
     int32_t sparse_div;
     int32_t sparse_iters;          // iterations graph 0 ran in push mode in this call
+    unsigned long long loop_kernels_total;  // device-loop kernel launches over all calls (never reset)
     Summary sum;
 };
 

@@ -215,6 +215,30 @@ def test_non_default_stream_and_launch_count():
         assert s.kernel_launches() == 4 + 5 * it
 
 
+@pytest.mark.parametrize("col_blocks", [1, 2])
+def test_launch_count_over_unsynchronised_calls(col_blocks):
+    """Calls issued back to back without a status check in between are all
+    counted: the device loop keeps a running total of its launches."""
+    import paper_1910_05971_gb300 as fsv
+    rp, ci = graphgen.rmat(12, 16, seed=6, permute=True)
+    _, it, _, _ = oracle.fastsv(rp, ci)
+    rp_d, ci_d = to_dev(rp), to_dev(ci)
+    with fsv.FastSV(col_blocks=col_blocks) as s:
+        lab = s.cc(rp_d, ci_d)
+        one = s.kernel_launches()
+        if col_blocks == 1:
+            assert one == 4 + 5 * it
+        else:
+            # set-up (3), the first iteration on the original CSR (4), the
+            # block build (11) and the blocks' set-up (3), finish (1); then
+            # 4 + col_blocks kernels per device-loop iteration
+            assert one == 22 + (4 + col_blocks) * (it - 1)
+        for _ in range(5):
+            s.cc(rp_d, ci_d, lab, check_status=False)
+        s.check_last()
+        assert s.kernel_launches() == 6 * one
+
+
 # ---------------------------------------------------------------------------
 # the named workloads at full size
 # ---------------------------------------------------------------------------
