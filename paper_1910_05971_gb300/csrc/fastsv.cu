@@ -578,10 +578,9 @@ static fastsv_status launch_block_build(fastsv_ctx* h, int nb, int shift, int64_
     FSV_CUDA(h, cudaFuncSetAttribute(fr, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_count));
     Ctx* ctx = h->d_ctx;
     int32_t* flag = h->d_sums + h->cap_sums - 1;  // "some row is not sorted by column"
-    long long* descents = h->d_build_scalars;
+    // the first iteration counted the rows' descending pairs
+    const unsigned long long* descents = h->d_build_scalars;
     int32_t* start = h->d_rpB;  // run starts of every (row, block)
-    FSV_CUDA(h, cudaMemsetAsync(descents, 0, sizeof(long long), s));
-    k_sorted_check<RP><<<g, 256, 0, s>>>(ctx, descents);
     k_sorted_result<<<1, 1, 0, s>>>(descents, flag);
     // sorted rows: run starts by binary search, counts as their differences
     k_block_runs<RP><<<g, 256, 0, s>>>(ctx, start, h->d_counts, nb, shift, flag);
@@ -612,7 +611,7 @@ static fastsv_status launch_block_build(fastsv_ctx* h, int nb, int shift, int64_
                      (void*)&shift, (void*)&flag};
         FSV_CUDA(h, cudaLaunchKernel(fr, dim3(g), dim3(BUILD_THREADS), a, (size_t)smem_count, s));
     }
-    h->pending_fixed_launches += 11;
+    h->pending_fixed_launches += 10;
     FSV_CUDA(h, cudaGetLastError());
     return FASTSV_OK;
 }
@@ -661,26 +660,30 @@ static fastsv_status ensure_block_workspace(fastsv_ctx* h, int nb, int64_t n, in
 
 // one iteration on segment 0's own tiles (BUILD_TILE items each), launched
 // kernel by kernel: the first iteration of a column-blocked solve.  Its SpMV
-// gathers nothing, so the per-tile merge-path search is most of its work: the
-// 64 x 16 instance spends one search on 16 items.
-static_assert(BUILD_TILE == 64 * 16, "first unblocked iteration runs the 64 x 16 SpMV instance");
+// (k2_first) gathers nothing, so the per-tile merge-path search is most of
+// its work: 64 threads x 16 items spend one search on 16 items.  It also
+// counts the rows' descending pairs for the block copy.
+static_assert(BUILD_TILE == FIRST_THREADS * FIRST_ITEMS, "the first iteration walks the build's tiles");
 static fastsv_status first_iteration_unblocked(fastsv_ctx* h, int rp64, cudaStream_t s) {
     IterKernels K;
     fastsv_status st = iter_kernels(h, rp64, rp64, 8, &K);
     if (st != FASTSV_OK) return st;
-    const void* spmv = k2_func(rp64, 16, 64);
-    const int smem = k2_smem(16, 64);
-    int grid = 0;
-    if ((st = k2_grid_for(h, rp64, 16, 64, &grid)) != FASTSV_OK) return st;
+    const void* spmv = rp64 ? (const void*)k2_first<int64_t> : (const void*)k2_first<int32_t>;
+    const int smem = k2_first_smem();
+    int per_sm = 0;
+    FSV_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, spmv, FIRST_THREADS, smem));
+    const int grid = (per_sm > 0 ? per_sm : 1) * h->num_sms;
     Ctx* ctx = h->d_ctx;
+    unsigned long long* descents = h->d_build_scalars;
+    FSV_CUDA(h, cudaMemsetAsync(descents, 0, sizeof(unsigned long long), s));
     cudaGraphConditionalHandle none = 0;
-    int no_cond = 0, blk = -1;
+    int no_cond = 0;
     void* a_begin[] = {(void*)&ctx, (void*)&none, (void*)&no_cond};
-    void* a_spmv[] = {(void*)&ctx, (void*)&blk};
+    void* a_spmv[] = {(void*)&ctx, (void*)&descents};
     void* a_ctx[] = {(void*)&ctx};
     void* a_k3[] = {(void*)&ctx, (void*)&none, (void*)&no_cond};
     FSV_CUDA(h, cudaLaunchKernel((const void*)k_iter_begin, dim3(K.vtx_grid), dim3(256), a_begin, 0, s));
-    FSV_CUDA(h, cudaLaunchKernel(spmv, dim3(grid), dim3(64), a_spmv, smem, s));
+    FSV_CUDA(h, cudaLaunchKernel(spmv, dim3(grid), dim3(FIRST_THREADS), a_spmv, smem, s));
     FSV_CUDA(h, cudaLaunchKernel(K.hook, dim3(K.vtx_grid), dim3(K3_THREADS), a_ctx, 0, s));
     FSV_CUDA(h, cudaLaunchKernel(K.k3, dim3(K.vtx_grid), dim3(K3_THREADS), a_k3, 0, s));
     h->pending_fixed_launches += 4;

@@ -64,7 +64,7 @@ struct fastsv_ctx {
     int64_t cap_sums = 0;
     int32_t* d_colB = nullptr;
     int64_t cap_colB = 0;
-    long long* d_build_scalars = nullptr;  // block build: descent counter
+    unsigned long long* d_build_scalars = nullptr;  // block build: descent counter
     int32_t* d_part_u0 = nullptr;           // block build: first row of every partition tile
     int64_t cap_part_u0 = 0;
     int64_t last_m_build = 0;

@@ -575,49 +575,14 @@ __global__ void __launch_bounds__(BUILD_THREADS)
 }
 
 // ---------------------------------------------------------------------------
-// column-block build for rows sorted by column (the common case): a
-// streaming sortedness test, run starts of every (row, block) by binary
-// search, and a stable partition of col_idx by block
+// column-block build for rows sorted by column (the common case): the
+// sortedness verdict (from the descending pairs the first iteration's SpMV
+// counted), run starts of every (row, block) by binary search, and a stable
+// partition of col_idx by block
 // ---------------------------------------------------------------------------
 
-// Sortedness test of the whole graph in two streaming passes: +1 for every
-// adjacent pair of entries in decreasing order (as unsigned ids, the order
-// the column blocks follow), -1 for every such pair that straddles a row
-// boundary (the last entry of one row before the first of the next
-// non-empty row).  The sum is zero exactly when every row is sorted.
-template <typename RP>
-__global__ void k_sorted_check(const Ctx* ctx, long long* descents) {
-    const Seg& S = ctx->segs[0];
-    const RP* rp = (const RP*)S.rp;
-    const uint32_t* ci = (const uint32_t*)S.ci;
-    const int64_t n = S.n, m = S.m;
-    long long d = 0;
-    const int64_t tid0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    // adjacent pairs (e, e+1): four entries per 16-byte load when col_idx is
-    // 16-byte aligned, the pair across each group from the next entry
-    int64_t e_tail = 0;
-    if ((reinterpret_cast<uintptr_t>(ci) & 15) == 0) {
-        const int64_t groups = m / 4;
-        const uint4* ci4 = reinterpret_cast<const uint4*>(ci);
-        for (int64_t g = tid0; g < groups; g += stride) {
-            const uint4 v = __ldcs(ci4 + g);
-            d += (v.x > v.y) + (v.y > v.z) + (v.z > v.w);
-            if (4 * g + 4 < m) d += v.w > __ldg(ci + 4 * g + 4);
-        }
-        e_tail = groups * 4;
-    }
-    for (int64_t e = e_tail + tid0; e + 1 < m; e += stride) d += ci[e] > ci[e + 1];
-    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x + 1; u < n; u += stride) {
-        const int64_t b = rp_at(rp, u);
-        if (b > 0 && b < m && b < rp_at(rp, u + 1)) d -= ci[b - 1] > ci[b];
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
-    if ((threadIdx.x & 31) == 0 && d) atomicAdd((unsigned long long*)descents, (unsigned long long)d);
-}
-
-__global__ void k_sorted_result(const long long* descents, int32_t* unsorted) { *unsorted = *descents != 0; }
+// the block copy's path: rows not all sorted (k2_first counted descending pairs)
+__global__ void k_sorted_result(const unsigned long long* descents, int32_t* unsorted) { *unsorted = *descents != 0; }
 
 // Sorted rows: start[k][u] = first position of row u whose column block is
 // >= k (the row end if none), found by binary search per (row, block)
@@ -1123,6 +1088,137 @@ __global__ void __launch_bounds__(THREADS) k2_spmv(Ctx* __restrict__ ctx, int bl
         __syncthreads();
     }
 }
+
+// a1 in the first iteration of a column-blocked solve, on the graph's own
+// CSR (segment 0, its merge-path tiles of FIRST_THREADS x FIRST_ITEMS
+// items): gf is still the identity (Algorithm 2 starts from f[u] = u), so
+// mngf[u] is u's smallest neighbour id and nothing is gathered.  The same
+// walk counts the adjacent entry pairs of a row that are in decreasing order
+// as unsigned ids into *descents (the pair that straddles a tile boundary
+// by the tile's first thread): zero exactly when every row is sorted, the
+// test that picks how the block copy is built.
+constexpr int FIRST_THREADS = 64;
+constexpr int FIRST_ITEMS = 16;
+
+template <typename RP>
+__global__ void __launch_bounds__(FIRST_THREADS)
+    k2_first(Ctx* __restrict__ ctx, unsigned long long* __restrict__ descents) {
+    constexpr int THREADS = FIRST_THREADS, ITEMS = FIRST_ITEMS, TILE = THREADS * ITEMS;
+    extern __shared__ int32_t smem[];
+    int32_t* s_rowend = smem;                // local end offset of each row in the tile
+    int32_t* s_mngf = smem + (TILE + 1);     // per-row minimum over the tile's entries
+    int32_t* s_col = smem + 2 * (TILE + 1);  // the tile's column ids as given
+    const int tid = threadIdx.x;
+    const Seg* __restrict__ S = ctx->segs;
+    const RP* __restrict__ rp = (const RP*)S->rp;
+    int32_t* mngf = S->mngf;
+    const int64_t n = S->n, m = S->m;
+    unsigned int desc = 0;
+    for (int64_t lt = blockIdx.x; lt < S->k2_ntiles; lt += gridDim.x) {
+        const int64_t t = S->k2_tile0 + lt;
+        const int64_t d0 = lt * TILE;
+        const int64_t d1 = min(d0 + (int64_t)TILE, n + m);
+        const int64_t x0 = ctx->k2_tile_row[t];
+        const int64_t x1 = (lt + 1 < S->k2_ntiles) ? (int64_t)ctx->k2_tile_row[t + 1] : n;
+        if (x1 < x0) continue;  // only possible for a malformed row_ptr
+        const int64_t y0 = d0 - x0, y1 = d1 - x1;
+        const int nfull = (int)(x1 - x0);
+        const int R = nfull + (x1 < n ? 1 : 0);
+        const int E = (int)(y1 - y0);
+        const int D = (int)(d1 - d0);
+        const RP* __restrict__ rpt = rp + x0 + 1;
+        const int32_t* __restrict__ cit = S->ci + y0;
+
+        for (int i = tid; i < R; i += THREADS) {
+            int64_t e = rp_at(rpt, i);
+            e = (e < y1 ? e : y1) - y0;
+            s_rowend[i] = (int32_t)(e < 0 ? 0 : e);
+            s_mngf[i] = INF;
+        }
+        {
+            int32_t c[ITEMS];
+#pragma unroll
+            for (int q = 0; q < ITEMS; ++q) {
+                const int j = tid + q * THREADS;
+                c[q] = j < E ? ld_stream(cit + j) : 0;
+            }
+#pragma unroll
+            for (int q = 0; q < ITEMS; ++q) {
+                const int j = tid + q * THREADS;
+                if (j < E) s_col[j] = c[q];
+            }
+        }
+        __syncthreads();
+
+        // the merge-path walk of k2_spmv over ITEMS items per thread; rstart
+        // is the tile-local first entry of the open row
+        const int k0 = tid * ITEMS;
+        int r = -1;
+        int32_t acc = INF;
+        if (k0 < D) {
+            int lo = 0, hi = nfull;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (s_rowend[mid] + mid < k0)
+                    lo = mid + 1;
+                else
+                    hi = mid;
+            }
+            r = lo;
+            int y = k0 - lo;
+            int rstart = lo > 0 ? s_rowend[lo - 1] : 0;
+            int rend = r < nfull ? s_rowend[r] : 0x7fffffff;
+            const int steps = min(ITEMS, D - k0);
+            for (int k = 0; k < steps; ++k) {
+                if (y >= rend) {
+                    if (acc != INF) atomicMin(&s_mngf[r], acc);
+                    acc = INF;
+                    ++r;
+                    rstart = rend;
+                    rend = r < nfull ? s_rowend[r] : 0x7fffffff;
+                } else {
+                    const int32_t v = s_col[y];
+                    if (y > rstart) desc += (uint32_t)s_col[y - 1] > (uint32_t)v;
+                    if ((uint32_t)v < (uint64_t)n) acc = min(acc, v);
+                    ++y;
+                }
+            }
+        }
+        {
+            const int key = (acc != INF && r >= 0 && r < R) ? r : -1;
+            const int key0 = __shfl_sync(0xffffffffu, key, 0);
+            if (__all_sync(0xffffffffu, key == key0)) {
+                const int32_t wmin = (int32_t)__reduce_min_sync(0xffffffffu, (unsigned)acc);
+                if ((tid & 31) == 0 && key0 >= 0) atomicMin(&s_mngf[key0], wmin);
+            } else if (key >= 0) {
+                atomicMin(&s_mngf[key], acc);
+            }
+        }
+        // the pair (y0 - 1, y0) when both lie in row x0 (a row that began in
+        // an earlier tile and still has an entry here)
+        const bool first_whole = rp_at(rp, x0) >= y0;
+        if (tid == 0 && !first_whole && E > 0 && (nfull == 0 || s_rowend[0] > 0))
+            desc += (uint32_t)__ldg(S->ci + y0 - 1) > (uint32_t)s_col[0];
+        __syncthreads();
+
+        // row minima into mngf: rows whole in the tile by plain stores, the
+        // first and last row (they may continue in a neighbouring tile) by
+        // atomic min
+        for (int i = tid; i < R; i += THREADS) {
+            const int32_t mn = s_mngf[i];
+            if (i < nfull && (i > 0 || first_whole))
+                mngf[x0 + i] = mn;
+            else if (mn != INF)
+                atomicMin(mngf + x0 + i, mn);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) desc += __shfl_down_sync(0xffffffffu, desc, o);
+    if ((tid & 31) == 0 && desc) atomicAdd(descents, (unsigned long long)desc);
+}
+
+__host__ __device__ constexpr int k2_first_smem() { return (3 * (FIRST_THREADS * FIRST_ITEMS) + 2) * (int)sizeof(int32_t); }
 
 // a1, sparse iteration (Section 4.2's SpMSpV): only vertices whose gf
 // changed in the last iteration can lower a neighbour's minimum, and gf never

@@ -91,6 +91,33 @@ def test_column_blocks_with_unsorted_rows():
         assert np.array_equal(got, f) and st["iterations"] == it and st["changed_per_iter"] == ch.tolist()
 
 
+@pytest.mark.parametrize("k", [2, 3])
+def test_column_blocks_with_one_descent_at_a_tile_boundary(k):
+    """The only unsorted pair of the graph lies in a hub row and straddles a
+    boundary of the 1024-item merge-path tiles the first iteration walks
+    (where the sortedness count reads the previous tile's last entry), with
+    its two ids in different column blocks: the block copy must notice it
+    and still reproduce Algorithm 2."""
+    n = 4096
+    row0 = [1] + list(range(3001, 4024))      # 1024 entries: the hub's row starts at entry 1024
+    hub = [0] + list(range(2, 3001))          # vertex 1
+    edges = [(0, v) for v in row0] + [(1, v) for v in hub[1:]] + [(4024 + i, 4025 + i) for i in range(0, 70, 2)]
+    rp, ci = oracle.csr_from_edges(n, edges)
+    ci = ci.copy()
+    assert rp[1] - rp[0] == 1024 and ci[rp[1]:rp[2]].tolist() == hub
+    # entry y of row u sits at merge-path diagonal u + y; a tile starts every
+    # 1024 diagonals, so hub entry j starts tile k for j = 1024k - 1025
+    j = 1024 * k - 1025
+    y = int(rp[1]) + j
+    assert (1 + y) % 1024 == 0
+    ci[y - 1], ci[y] = ci[y], ci[y - 1]
+    assert ci[y - 1] // 1024 != ci[y] // 1024      # 4 blocks of 1024 ids
+    f, it, _, ch = oracle.fastsv(rp, ci)
+    for nb in (1, 4):
+        got, st = gpu_solve(rp, ci, col_blocks=nb)
+        assert np.array_equal(got, f) and st["iterations"] == it and st["changed_per_iter"] == ch.tolist()
+
+
 def test_host_loop_mode_matches():
     rp, ci = graphgen.rmat(13, 8, seed=2, permute=True)
     f, it, _, ch = oracle.fastsv(rp, ci)
@@ -230,9 +257,9 @@ def test_launch_count_over_unsynchronised_calls(col_blocks):
             assert one == 4 + 5 * it
         else:
             # set-up (3), the first iteration on the original CSR (4), the
-            # block build (11) and the blocks' set-up (3), finish (1); then
+            # block build (10) and the blocks' set-up (3), finish (1); then
             # 4 + col_blocks kernels per device-loop iteration
-            assert one == 22 + (4 + col_blocks) * (it - 1)
+            assert one == 21 + (4 + col_blocks) * (it - 1)
         for _ in range(5):
             s.cc(rp_d, ci_d, lab, check_status=False)
         s.check_last()
