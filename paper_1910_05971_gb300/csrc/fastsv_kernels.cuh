@@ -1093,10 +1093,11 @@ __global__ void __launch_bounds__(THREADS) k2_spmv(Ctx* __restrict__ ctx, int bl
 // CSR (segment 0, its merge-path tiles of FIRST_THREADS x FIRST_ITEMS
 // items): gf is still the identity (Algorithm 2 starts from f[u] = u), so
 // mngf[u] is u's smallest neighbour id and nothing is gathered.  The same
-// walk counts the adjacent entry pairs of a row that are in decreasing order
-// as unsigned ids into *descents (the pair that straddles a tile boundary
-// by the tile's first thread): zero exactly when every row is sorted, the
-// test that picks how the block copy is built.
+// pass counts into *descents the adjacent entry pairs of a row that are in
+// decreasing order as unsigned ids: every adjacent pair ending in the tile
+// (striped over the threads, off the walk's serial loop), minus the pairs
+// that end at a row's first entry.  Zero exactly when every row is sorted,
+// the test that picks how the block copy is built.
 constexpr int FIRST_THREADS = 64;
 constexpr int FIRST_ITEMS = 16;
 
@@ -1113,7 +1114,7 @@ __global__ void __launch_bounds__(FIRST_THREADS)
     const RP* __restrict__ rp = (const RP*)S->rp;
     int32_t* mngf = S->mngf;
     const int64_t n = S->n, m = S->m;
-    unsigned int desc = 0;
+    int desc = 0;
     for (int64_t lt = blockIdx.x; lt < S->k2_ntiles; lt += gridDim.x) {
         const int64_t t = S->k2_tile0 + lt;
         const int64_t d0 = lt * TILE;
@@ -1166,7 +1167,6 @@ __global__ void __launch_bounds__(FIRST_THREADS)
             }
             r = lo;
             int y = k0 - lo;
-            int rstart = lo > 0 ? s_rowend[lo - 1] : 0;
             int rend = r < nfull ? s_rowend[r] : 0x7fffffff;
             const int steps = min(ITEMS, D - k0);
             for (int k = 0; k < steps; ++k) {
@@ -1174,11 +1174,9 @@ __global__ void __launch_bounds__(FIRST_THREADS)
                     if (acc != INF) atomicMin(&s_mngf[r], acc);
                     acc = INF;
                     ++r;
-                    rstart = rend;
                     rend = r < nfull ? s_rowend[r] : 0x7fffffff;
                 } else {
                     const int32_t v = s_col[y];
-                    if (y > rstart) desc += (uint32_t)s_col[y - 1] > (uint32_t)v;
                     if ((uint32_t)v < (uint64_t)n) acc = min(acc, v);
                     ++y;
                 }
@@ -1194,11 +1192,19 @@ __global__ void __launch_bounds__(FIRST_THREADS)
                 atomicMin(&s_mngf[key], acc);
             }
         }
-        // the pair (y0 - 1, y0) when both lie in row x0 (a row that began in
-        // an earlier tile and still has an entry here)
+        // descending pairs: every adjacent pair ending in this tile, minus
+        // those that cross into a row's first entry
         const bool first_whole = rp_at(rp, x0) >= y0;
-        if (tid == 0 && !first_whole && E > 0 && (nfull == 0 || s_rowend[0] > 0))
-            desc += (uint32_t)__ldg(S->ci + y0 - 1) > (uint32_t)s_col[0];
+        const uint32_t before = (y0 > 0 && E > 0) ? (uint32_t)__ldg(S->ci + y0 - 1) : 0u;
+        for (int j = tid; j < E; j += THREADS)
+            desc += (int)((j > 0 ? (uint32_t)s_col[j - 1] : before) > (uint32_t)s_col[j]);
+        for (int i = tid; i < R; i += THREADS) {
+            if (i == 0 && !first_whole) continue;  // row x0 began in an earlier tile
+            const int st = i == 0 ? 0 : s_rowend[i - 1];
+            const int en = i < nfull ? s_rowend[i] : E;
+            if (st < en && y0 + st > 0)
+                desc -= (int)((st > 0 ? (uint32_t)s_col[st - 1] : before) > (uint32_t)s_col[st]);
+        }
         __syncthreads();
 
         // row minima into mngf: rows whole in the tile by plain stores, the
@@ -1215,7 +1221,7 @@ __global__ void __launch_bounds__(FIRST_THREADS)
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) desc += __shfl_down_sync(0xffffffffu, desc, o);
-    if ((tid & 31) == 0 && desc) atomicAdd(descents, (unsigned long long)desc);
+    if ((tid & 31) == 0 && desc) atomicAdd(descents, (unsigned long long)(long long)desc);
 }
 
 __host__ __device__ constexpr int k2_first_smem() { return (3 * (FIRST_THREADS * FIRST_ITEMS) + 2) * (int)sizeof(int32_t); }
