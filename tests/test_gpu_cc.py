@@ -143,8 +143,9 @@ def test_edge_cases():
     edges = sorted({(int(a), int(b)) for a, b in zip(rng.integers(400, size=300), rng.integers(400, size=300)) if a < b})
     noisy = edges + edges[:50] + [(i, i) for i in range(0, 400, 9)]
     f, it, _, ch = oracle.fastsv(*oracle.csr_from_edges(400, edges))
-    got, st = gpu_solve(*oracle.csr_from_edges(400, noisy))
-    assert np.array_equal(got, f) and st["iterations"] == it and st["changed_per_iter"] == ch.tolist()
+    for nb in (1, 4):  # also through the column-block copy (rows with repeated ids count as sorted)
+        got, st = gpu_solve(*oracle.csr_from_edges(400, noisy), col_blocks=nb)
+        assert np.array_equal(got, f) and st["iterations"] == it and st["changed_per_iter"] == ch.tolist()
 
 
 def test_iteration_cap_reports_partial_state():
