@@ -576,7 +576,7 @@ __global__ void __launch_bounds__(BUILD_THREADS)
 
 // ---------------------------------------------------------------------------
 // column-block build for rows sorted by column (the common case): the
-// sortedness verdict (from the descending pairs the first iteration's SpMV
+// sortedness result (from the descending pairs the first iteration's SpMV
 // counted), run starts of every (row, block) by binary search, and a stable
 // partition of col_idx by block
 // ---------------------------------------------------------------------------
