@@ -94,7 +94,11 @@ typedef struct {
                               gathered vector), 1 = never, 2..16 = that many.  A blocked call copies
                               col_idx once into column-block order (needs m <= 2^31 - 1 and 4m + 8nb(n+1)
                               bytes of workspace) and runs one SpMV launch per block, whose gathers
-                              then hit an L2-resident slice of the grandparent vector */
+                              then hit an L2-resident slice of the grandparent vector.  Its first
+                              iteration runs before the copy, on the caller's CSR (it gathers nothing),
+                              and also tests whether every row is sorted by column: sorted rows are
+                              copied by a stable partition, others by a ranked scatter (slower; both
+                              give the same labels and iterations) */
     int32_t k2_threads;    /* threads per CTA of the SpMV kernel: 256 (default) or 64 */
     int32_t sparse_div;    /* single-graph calls: an iteration pushes from the vertices whose grandparent
                               changed (SpMSpV, Section 4.2) instead of a full SpMV when the degree sum of
