@@ -29,9 +29,7 @@ import argparse
 import hashlib
 import json
 import os
-import subprocess
 import sys
-import threading
 import time
 
 import numpy as np
@@ -41,6 +39,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 import graphgen  # noqa: E402
+from paper_1910_05971_gb300.clocks import ClockSampler  # noqa: E402,F401
 
 WORKLOADS = {
     "rmat_s26_perm": dict(desc="R-MAT scale 26, edge factor 16, a/b/c=.57/.19/.19, ids permuted, seed 3",
@@ -93,65 +92,6 @@ def profiled_traffic(workload: str):
         return float(rows["dram_bytes_per_launch"])
     except Exception:
         return None
-
-
-class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
-
-    def __init__(self, gpu_index: int):
-        self.gpu = gpu_index
-        self.proc = None
-        self.lines = []
-
-    def start(self):
-        try:
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.thread = threading.Thread(target=self._read, daemon=True)
-            self.thread.start()
-        except Exception:
-            self.proc = None
-
-    def _read(self):
-        for line in self.proc.stdout:
-            self.lines.append(line.strip())
-
-    def stop(self):
-        if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except Exception:
-            self.proc.kill()
-        return self.summarize(self.lines)
-
-    @classmethod
-    def summarize(cls, lines):
-        """Median SM clock, highest max clock and every throttle reason seen
-        Active, from CSV lines in the order of FIELDS (malformed lines skipped)."""
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in lines:
-            parts = [x.strip() for x in ln.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower() == "active":
-                    reasons.add(nm)
-        if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "samples": len(sm),
-                "reasons": sorted(reasons)}
 
 
 def make_graph(workload: str):

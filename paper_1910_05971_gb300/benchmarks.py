@@ -25,8 +25,7 @@ def _log(*a):
 
 
 def _clock_sampler(local_rank):
-    sys.path.insert(0, __import__("os").path.dirname(__import__("os").path.dirname(__file__)))
-    from bench import ClockSampler
+    from .clocks import ClockSampler
     return ClockSampler(local_rank)
 
 
