@@ -49,7 +49,7 @@ WORKLOADS = {
                               bits=64),
     "grid_4096_p055_iso1M": dict(desc="4096x4096 lattice, p=0.55, +1M isolated, seed 2", bits=32),
 }
-METRIC = "CC |E|/s (GTEPS) + %HBM peak at R-MAT s26"
+METRIC = "CC |E|/s (GTEPS) + %HBM peak at R-MAT s26; batched graphs/s; serve p50/p99"
 
 
 def log(*a):
@@ -71,8 +71,9 @@ def kernel_source_hash() -> str:
     p = os.path.join(ROOT, "paper_1910_05971_gb300", "csrc", "fastsv_kernels.cuh")
     with open(p) as fh:
         src = fh.read()
-    start = src.index("template <typename RP, int THREADS, int ITEMS>\n__global__ void __launch_bounds__(THREADS) k2_spmv")
-    end = src.index("\n}\n", start) + 3
+    sig = src.index(" k2_spmv(Ctx* __restrict__ ctx, int block) {")
+    start = src.rindex("template <", 0, sig)
+    end = src.index("\n}\n", sig) + 3
     return hashlib.sha256(src[start:end].encode()).hexdigest()[:16]
 
 
@@ -139,7 +140,11 @@ def main():
     ap.add_argument("--variant-workloads", default="rmat_s16,grid_4096_p055_iso1M,rmat_s26_perm",
                     help="variants mode: comma-separated workloads")
     ap.add_argument("--graphs", type=int, default=4096, help="batched mode: number of graphs")
-    ap.add_argument("--requests", type=int, default=256, help="serve mode: trace prefix length")
+    ap.add_argument("--requests", type=int, default=1024, help="serve: arrivals of the trace replayed")
+    ap.add_argument("--distinct", type=int, default=256,
+                    help="serve: distinct request graphs materialised (arrival i carries graph i mod this)")
+    ap.add_argument("--no-batched", action="store_true", help="single mode: leave out the batched measurement")
+    ap.add_argument("--no-serve", action="store_true", help="single mode: leave out the serving measurement")
     ap.add_argument("--batch-sparse-div", type=int, default=0,
                     help="batched/serve modes: per-graph sparse iterations threshold (0 = off)")
     args = ap.parse_args()
@@ -150,6 +155,8 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
 
+    peaks, peak_src = measured_peaks()
+    args.peak_gbs, args.peak_source = float(peaks["hbm_gbs"]), f"{peak_src} hbm_gbs"
     if args.impl == "reference":
         return run_reference(args, rank, world)
     if args.mode == "batched":
@@ -292,6 +299,27 @@ def main():
                "seconds": secs}
 
     solver.close()
+    del rp_dev, ci_dev, labels
+    torch.cuda.empty_cache()
+
+    # ---- the other two parts of the metric: batched graphs/s, serve p50/p99 ----
+    from paper_1910_05971_gb300 import benchmarks as bench_modes
+    batched = serve = None
+    if not args.no_batched:
+        try:
+            batched = bench_modes.batched_measure(args.graphs, max(3, args.steps // 2), args.warmup, args.k2_items,
+                                                  args.batch_sparse_div, local_rank, dist, rank, world,
+                                                  sampler=ClockSampler(local_rank), peak_gbs=args.peak_gbs,
+                                                  peak_source=args.peak_source)
+        except Exception as e:  # reported in the line; the headline stands on its own
+            batched = {"error": f"{type(e).__name__}: {e}"}
+        torch.cuda.empty_cache()
+    if not args.no_serve and rank == 0:
+        try:
+            serve = bench_modes.serve_measure(args.requests, args.distinct, args.k2_items, args.batch_sparse_div,
+                                              sampler=ClockSampler(local_rank))
+        except Exception as e:
+            serve = {"error": f"{type(e).__name__}: {e}"}
     if rank == 0:
         out = {
             "metric": METRIC,
@@ -326,6 +354,8 @@ def main():
             "e2e": e2e,
             "gpu_launches": int(launches),
             "clocks": clocks,
+            "batched": batched,
+            "serve": serve,
         }
         print(json.dumps(out), flush=True)
     if dist is not None:

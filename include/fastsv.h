@@ -85,20 +85,21 @@ typedef struct {
                               0: host loop, one synchronisation per iteration, per-kernel timings */
     int32_t k2_items;      /* merge-path items per thread in the hooking kernel (0 = default) */
     int32_t grid_ctas_per_sm; /* persistent CTAs per SM for the iteration kernels (0 = occupancy limit) */
-    int32_t l2_persist;    /* 1: mark the gathered grandparent vector as persisting in L2 (default 0) */
     int32_t timing;        /* 1: record device time of each call with CUDA events (default 1) */
     int32_t fail_alloc_after; /* test hook: >0 makes the N-th workspace allocation of this handle fail
                                  (returns FASTSV_ERR_OOM); 0 off */
     int32_t col_blocks;    /* column blocks of the SpMV for one large graph: 0 = automatic (blocks when
-                              4n bytes >= 1.5x the L2 and m >= 8n, one block per 64 MiB of the
-                              gathered vector), 1 = never, 2..16 = that many.  A blocked call copies
-                              col_idx once into column-block order (needs m <= 2^31 - 1 and 4m + 8nb(n+1)
-                              bytes of workspace) and runs one SpMV launch per block, whose gathers
-                              then hit an L2-resident slice of the grandparent vector.  Its first
-                              iteration runs before the copy, on the caller's CSR (it gathers nothing),
-                              and also tests whether every row is sorted by column: sorted rows are
-                              copied by a stable partition, others by a ranked scatter (slower; both
-                              give the same labels and iterations) */
+                              4n bytes >= 1.5x the L2 and m >= 8n, one block per col_block_mib MiB of the
+                              gathered vector), 1 = never, 2..32 = that many.  A blocked call copies
+                              col_idx once into column-block order (needs m <= 2^31 - 1) and runs one
+                              SpMV launch per block, whose gathers then hit an L2-resident slice of the
+                              grandparent vector.  A block lists only the rows that have entries in it
+                              (compressed rows).  Its first iteration runs before the copy, on the
+                              caller's CSR (it gathers nothing), and counts the copy's sizes; the call
+                              then synchronises once more, to size the copy's row lists (workspace:
+                              4m bytes of entries, 8 bytes per (row, block) pair, 8nb bytes per 1024
+                              entries of counts).  Rows need not be sorted (unsorted rows give longer
+                              row lists and slower merges, never other labels) */
     int32_t k2_threads;    /* threads per CTA of the SpMV kernel: 256 (default) or 64 */
     int32_t sparse_div;    /* single-graph calls: an iteration pushes from the vertices whose grandparent
                               changed (SpMSpV, Section 4.2) instead of a full SpMV when the degree sum of
@@ -115,7 +116,16 @@ typedef struct {
                               m_graph / batch_sparse_div; 0 (default) = always full SpMV.  Off by default:
                               on 4096 ER graphs the frontier bookkeeping cost more than the pushes saved
                               (139k graphs/s off, 116k at 4 to 32, 101k at 2) */
-    int32_t reserved[1];
+    int32_t col_block_mib; /* automatic column blocking (col_blocks = 0): MiB of the grandparent vector per
+                              block (default 32, about a quarter of the L2) */
+    int32_t pool_wait_copies; /* pools: 0 (default) = a graph joins the first step after its copies to the
+                              device have landed (copies overlap iterations); 1 = every step waits for the
+                              copies of all graphs admitted before it, so a graph added before a step
+                              always takes part in it */
+    const char* tune_cache; /* NULL (default) or the path of a tuning cache written by the autotuner: for a
+                              graph whose shape class (fastsv_tune_key) has an entry, the entry's k2_items,
+                              k2_threads, col_blocks, sparse_div and batch_sparse_div replace the values above.
+                              The file is read once, by fastsv_create; an unreadable file is an argument error */
 } fastsv_options;
 
 typedef struct {
@@ -141,7 +151,23 @@ typedef struct {
                                   original CSR (no gathers are needed while gf is the identity); that
                                   iteration is part of ms_setup */
     int32_t timed_dense_iters; /* host-loop mode: of those, the iterations that ran the full SpMV */
+    int32_t tuned;             /* 1 if the last call took its kernel choices from the tuning cache */
+    int32_t pad0;
+    int64_t block_runs;        /* column-blocked single-graph calls: runs (compressed rows) over all blocks */
 } fastsv_stats;
+
+/*
+ * Shape class of a call, as the tuning cache keys it: kind 0 = single graph
+ * (n vertices, m entries, rowptr_bits), kind 1 = batched call (n and m summed
+ * over `graphs` graphs).  Writes a NUL-terminated string such as
+ * "single n26 d10 r64" (log2 of n rounded; half-octaves of m/n) into out[cap]
+ * and returns its length, or -1 for a bad argument.  The autotuner writes
+ * cache lines under these keys; fastsv_cc, fastsv_cc_host and
+ * fastsv_cc_batched look them up.  Pools do not: they run the handle's own
+ * options.
+ */
+int32_t fastsv_tune_key(int32_t kind, int64_t n, int64_t m, int64_t graphs, int32_t rowptr_bits, char* out,
+                        int32_t cap);
 
 /* Fill *opt with the defaults listed above. */
 void fastsv_default_options(fastsv_options* opt);
@@ -164,8 +190,10 @@ fastsv_status fastsv_destroy(fastsv_t h);
  *              vertex's component.  It also serves as the parent vector f
  *              during the solve, so it must not alias row_ptr or col_idx.
  *   stream     cudaStream_t
- * Synchronises with `stream` once, to read m = row_ptr[n].  The solve itself
- * is enqueued; labels_out is valid when the stream reaches the end of it.
+ * Synchronises with `stream` once, to read m = row_ptr[n] (a column-blocked
+ * call once more, after its first iteration: see col_blocks).  The rest of
+ * the solve is enqueued; labels_out is valid when the stream reaches the end
+ * of it.
  */
 fastsv_status fastsv_cc(fastsv_t h, int64_t n, const void* row_ptr, const int32_t* col_idx, int32_t* labels_out,
                         void* stream);
@@ -244,8 +272,12 @@ fastsv_status fastsv_pool_add(fastsv_t h, int64_t n, const int32_t* row_ptr_host
                               int32_t* labels_host, int32_t* slot_out);
 
 /* Advance every active slot by up to `iters` iterations (iters >= 1) on
- * `stream`.  Slots admitted since the last step join this one (the step
- * waits for their copies).  Enqueued; returns at once. */
+ * `stream`.  Slots admitted earlier whose copies to the device have landed
+ * join this step; slots whose copies are still running keep copying while it
+ * runs and join a later step (so copies overlap iterations).  A step with no
+ * resident graph waits for the first admitted graph's copies instead.  With
+ * opt.pool_wait_copies = 1 every admitted slot joins (the step waits for all
+ * their copies).  Enqueued; returns at once. */
 fastsv_status fastsv_pool_step(fastsv_t h, int32_t iters, void* stream);
 
 /*
@@ -260,9 +292,10 @@ fastsv_status fastsv_pool_poll(fastsv_t h, int32_t* done_slots, int32_t* done_it
                                int32_t* n_active);
 
 /* Device time of the last step's phases (timing = 1): ms_out[0] waiting for
- * the copies of graphs admitted since the step before, ms_out[1] admitting
- * them and rebuilding the tile lists, ms_out[2] the iterations.  Waits for
- * the step; all zero when timing is off. */
+ * admission copies (only a step that had nothing else to run waits),
+ * ms_out[1] admitting the joining graphs and rebuilding the tile lists,
+ * ms_out[2] the iterations.  Waits for the step; all zero when timing is
+ * off. */
 fastsv_status fastsv_pool_step_times(fastsv_t h, float* ms_out);
 
 /* Pool occupancy: slots in use and bytes of the budget in use. */
@@ -334,12 +367,20 @@ fastsv_status fastsv_pool_restore(fastsv_t h, int64_t n, const int32_t* row_ptr_
  *   stream     cudaStream_t
  * Calls no cudaMalloc, cudaFree or other allocating routine.  The first call
  * on each device looks up the scratch array's device address (with that
- * device current) and caches it; make that first call before any stream
- * capture.  All calls on a device share the one scratch array, which keeps
- * the previous call's contents (every call re-initialises what it reads):
- * calls that overlap on the GPU, from any thread or stream, race on it and
- * must be serialised by the caller.  Synchronises with `stream` once per
- * iteration; returns when labels_out is final.
+ * device current) and caches it.  With lazy module loading (the CUDA
+ * default) the library's device code, the scratch array included, is
+ * loaded by that first call and takes device memory then: make the first
+ * call (or load the library with CUDA_MODULE_LOADING=EAGER) before reserving
+ * the device memory the caller wants to keep for itself.  The call
+ * synchronises with `stream` once per iteration, so it must not be called
+ * while `stream` is being captured.  All calls on a device share the one
+ * scratch array, which keeps the previous call's contents (every call
+ * re-initialises what it reads): calls that overlap on the GPU, from any
+ * thread or stream, race on it and must be serialised by the caller.
+ * The CSR is not validated: row_ptr must be non-decreasing with
+ * row_ptr[0] = 0, and col_idx must hold row_ptr[n] ids; neighbour ids
+ * outside [0, n) are skipped, but a malformed row_ptr makes the kernels
+ * read col_idx out of bounds.  Returns when labels_out is final.
  */
 fastsv_status fastsv_cc_noalloc(int64_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t* labels_out,
                                 int32_t max_iters, int32_t* iterations_out, void* stream);

@@ -15,6 +15,7 @@ used only for device memory and streams; the arithmetic runs in libfastsv.
 from __future__ import annotations
 
 import ctypes as C
+import os
 
 from . import _lib
 from ._lib import (  # noqa: F401  (re-exported C names)
@@ -26,7 +27,12 @@ from ._lib import (  # noqa: F401  (re-exported C names)
     fastsv_pool_create, fastsv_pool_bytes, fastsv_pool_add, fastsv_pool_step, fastsv_pool_poll,
     fastsv_pool_usage, load, library_path, fastsv_cc_noalloc, FASTSV_NOALLOC_MAX_VERTICES,
     fastsv_pool_checkpoint_bytes, fastsv_pool_evict, fastsv_pool_restore, fastsv_pool_step_times,
+    fastsv_tune_key, TUNE_SINGLE, TUNE_BATCHED,
 )
+
+# the tuning cache the autotuner (tune.py) wrote on GB300 for the shape
+# classes of the standard workloads; handles use it unless told otherwise
+DEFAULT_TUNE_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tune_cache.txt")
 
 
 def _torch():
@@ -47,16 +53,23 @@ def stats_dict(s: fastsv_stats) -> dict:
                 ms_total=s.ms_total, ms_setup=s.ms_setup, ms_k2=s.ms_k2, ms_k3=s.ms_k3, ms_push=s.ms_push,
                 ms_hook=s.ms_hook, sparse_iters=s.sparse_iters, dense_iters=s.dense_iters,
                 col_blocks=s.col_blocks, changed_per_iter=[int(s.changed_per_iter[i]) for i in range(s.trace_len)],
-                timed_iters=s.timed_iters, timed_dense_iters=s.timed_dense_iters)
+                timed_iters=s.timed_iters, timed_dense_iters=s.timed_dense_iters, tuned=bool(s.tuned),
+                block_runs=s.block_runs)
 
 
 class FastSV:
-    """One library handle (one workspace).  Not thread-safe."""
+    """One library handle (one workspace).  Not thread-safe.
+
+    ``tune_cache``: path of a tuning cache ("default": the packaged cache, if
+    present; None: none), whose entries replace k2_items, k2_threads,
+    col_blocks, sparse_div and batch_sparse_div for the shape classes they
+    cover."""
 
     def __init__(self, rowptr_bits: int = 64, mode: int = FASTSV_MODE_SYNC, max_iters: int = 4096,
                  validate: int = 0, use_graph: bool = True, k2_items: int = 8, grid_ctas_per_sm: int = 0,
-                 l2_persist: bool = False, timing: bool = True, fail_alloc_after: int = 0, col_blocks: int = 0,
-                 k2_threads: int = 256, sparse_div: int = 2, variant: int = 0, batch_sparse_div: int = 0):
+                 timing: bool = True, fail_alloc_after: int = 0, col_blocks: int = 0,
+                 k2_threads: int = 256, sparse_div: int = 2, variant: int = 0, batch_sparse_div: int = 0,
+                 col_block_mib: int = 32, pool_wait_copies: bool = False, tune_cache: str | None = "default"):
         _torch()
         o = fastsv_default_options()
         o.rowptr_bits = rowptr_bits
@@ -66,7 +79,6 @@ class FastSV:
         o.use_graph = int(use_graph)
         o.k2_items = k2_items
         o.grid_ctas_per_sm = grid_ctas_per_sm
-        o.l2_persist = int(l2_persist)
         o.timing = int(timing)
         o.fail_alloc_after = fail_alloc_after
         o.col_blocks = col_blocks
@@ -74,6 +86,12 @@ class FastSV:
         o.sparse_div = sparse_div
         o.variant = variant
         o.batch_sparse_div = batch_sparse_div
+        o.col_block_mib = col_block_mib
+        o.pool_wait_copies = int(pool_wait_copies)
+        if tune_cache == "default":
+            tune_cache = DEFAULT_TUNE_CACHE if os.path.exists(DEFAULT_TUNE_CACHE) else None
+        self._tune_path = tune_cache.encode() if tune_cache else None  # kept alive for the call below
+        o.tune_cache = self._tune_path
         self.options = o
         self.h = fastsv_create(o)
 

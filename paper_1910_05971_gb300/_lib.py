@@ -42,7 +42,6 @@ class fastsv_options(C.Structure):
         ("use_graph", C.c_int32),
         ("k2_items", C.c_int32),
         ("grid_ctas_per_sm", C.c_int32),
-        ("l2_persist", C.c_int32),
         ("timing", C.c_int32),
         ("fail_alloc_after", C.c_int32),
         ("col_blocks", C.c_int32),
@@ -50,7 +49,9 @@ class fastsv_options(C.Structure):
         ("sparse_div", C.c_int32),
         ("variant", C.c_int32),
         ("batch_sparse_div", C.c_int32),
-        ("reserved", C.c_int32 * 1),
+        ("col_block_mib", C.c_int32),
+        ("pool_wait_copies", C.c_int32),
+        ("tune_cache", C.c_char_p),
     ]
 
 
@@ -74,6 +75,9 @@ class fastsv_stats(C.Structure):
         ("changed_per_iter", C.c_int64 * 64),
         ("timed_iters", C.c_int32),
         ("timed_dense_iters", C.c_int32),
+        ("tuned", C.c_int32),
+        ("pad0", C.c_int32),
+        ("block_runs", C.c_int64),
     ]
 
 
@@ -110,6 +114,7 @@ _SIGNATURES = [
     ("fastsv_pool_evict", C.c_int, [_P, C.c_int32, _P]),
     ("fastsv_pool_restore", C.c_int, [_P, C.c_int64, _P, _P, _P, _P, C.POINTER(C.c_int32)]),
     ("fastsv_cc_noalloc", C.c_int, [C.c_int64, _P, _P, _P, C.c_int32, C.POINTER(C.c_int32), _P]),
+    ("fastsv_tune_key", C.c_int32, [C.c_int32, C.c_int64, C.c_int64, C.c_int64, C.c_int32, C.c_char_p, C.c_int32]),
 ]
 
 # largest vertex count of fastsv_cc_noalloc (FASTSV_NOALLOC_MAX_VERTICES)
@@ -265,3 +270,16 @@ def fastsv_cc_noalloc(n: int, row_ptr: int, col_idx: int | None, labels_out: int
     it = C.c_int32(0)
     st = _call("fastsv_cc_noalloc", n, row_ptr, col_idx, labels_out, max_iters, C.byref(it), stream)
     return st, it.value
+
+
+TUNE_SINGLE = 0
+TUNE_BATCHED = 1
+
+
+def fastsv_tune_key(kind: int, n: int, m: int, graphs: int = 1, rowptr_bits: int = 64) -> str:
+    """Shape-class key of the tuning cache (see include/fastsv.h)."""
+    buf = C.create_string_buffer(128)
+    k = _call("fastsv_tune_key", kind, n, m, graphs, rowptr_bits, buf, 128)
+    if k < 0:
+        raise ValueError("fastsv_tune_key: bad argument")
+    return buf.value.decode()

@@ -29,20 +29,22 @@ def _clock_sampler(local_rank):
     return ClockSampler(local_rank)
 
 
-def run_batched(args, rank, world, local_rank):
+def batched_measure(graphs: int, steps: int, warmup: int, k2_items: int = 8, batch_sparse_div: int = 0,
+                    local_rank: int = 0, dist=None, rank: int = 0, world: int = 1, sampler=None,
+                    peak_gbs: float | None = None, peak_source: str = "") -> dict:
+    """Config 4: one segmented solve of `graphs` Erdos-Renyi graphs (one device
+    loop for the whole batch, each graph stopping at its own early
+    termination) against the same graphs solved by per-graph fastsv_cc calls
+    on the same GPU.  Both must give identical labels and iteration counts.
+    Also the batched SpMV's counted bytes over its time (host-loop pass)."""
     import torch
 
     import graphgen
     import paper_1910_05971_gb300 as fsv
     from paper_1910_05971_gb300.replicas import batch_work, max_over_ranks, shard_graphs
 
-    torch.cuda.set_device(local_rank)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     t0 = time.time()
-    full = graphgen.er_batch(args.graphs, seed=4)
+    full = graphgen.er_batch(graphs, seed=4)
     if world > 1:
         mine = shard_graphs(batch_work(full), world)[rank]
         batch = graphgen.Batch.from_graphs([full.graph(g) for g in mine])
@@ -53,33 +55,47 @@ def run_batched(args, rank, world, local_rank):
     _log(f"[bench] batch of {G} graphs, n={N} m={M}, generated in {time.time() - t0:.1f}s")
     d = {k: torch.from_numpy(getattr(batch, k)).cuda() for k in ("vtx_off", "edge_off", "row_ptr", "col_idx")}
     stream = torch.cuda.current_stream()
-    solver = fsv.FastSV(rowptr_bits=32, k2_items=args.k2_items, batch_sparse_div=args.batch_sparse_div)
+    solver = fsv.FastSV(rowptr_bits=32, k2_items=k2_items, batch_sparse_div=batch_sparse_div)
     labels = torch.empty(N, dtype=torch.int32, device="cuda")
     iters = torch.empty(G, dtype=torch.int32, device="cuda")
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         solver.cc_batched(d["vtx_off"], d["edge_off"], d["row_ptr"], d["col_idx"], labels, iters)
+    tuned = solver.stats()["tuned"]
     launches0 = solver.kernel_launches()
-    sampler = _clock_sampler(local_rank)
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
-    sampler.start()
+    if sampler is not None:
+        sampler.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         solver.cc_batched(d["vtx_off"], d["edge_off"], d["row_ptr"], d["col_idx"], labels, iters,
                           check_status=False)
     e1.record(stream)
     torch.cuda.synchronize()
-    clocks = sampler.stop()
+    clocks = sampler.stop() if sampler is not None else None
     solver.check_last()
-    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist)
+    ms = max_over_ranks(e0.elapsed_time(e1) / steps, dist)
     launches = solver.kernel_launches() - launches0
+    solver.close()
     lab_b = labels.cpu().numpy()
     it_b = iters.cpu().numpy()
 
+    # the batched SpMV alone: host-loop pass with per-kernel events; every
+    # graph runs one full SpMV per iteration it takes (no sparse iterations
+    # unless batch_sparse_div), so its counted bytes are summed per graph
+    prof = fsv.FastSV(rowptr_bits=32, k2_items=k2_items, batch_sparse_div=batch_sparse_div, use_graph=False)
+    prof.cc_batched(d["vtx_off"], d["edge_off"], d["row_ptr"], d["col_idx"], labels, iters)
+    sp = prof.stats()
+    prof.close()
+    n_g = np.diff(batch.vtx_off)
+    m_g = np.diff(batch.edge_off)
+    spmv_bytes = float(np.sum(it_b.astype(np.float64) * (4 * (n_g + 1) + 8 * m_g + 4 * n_g)))
+    spmv_ms = sp["ms_k2"] if batch_sparse_div == 0 else None
+
     # per-graph plain launches of the same kernels, one graph after another
-    plain = fsv.FastSV(rowptr_bits=32, k2_items=args.k2_items)
+    plain = fsv.FastSV(rowptr_bits=32, k2_items=k2_items)
     vo, eo = batch.vtx_off, batch.edge_off
     lab_p = torch.empty(N, dtype=torch.int32, device="cuda")
     it_p = np.zeros(G, dtype=np.int64)
@@ -100,23 +116,54 @@ def run_batched(args, rank, world, local_rank):
     torch.cuda.synchronize()
     plain_s = max_over_ranks(time.perf_counter() - t, dist)
     same = bool(np.array_equal(lab_p.cpu().numpy(), lab_b)) and bool(np.array_equal(it_p, it_b))
-    total_graphs = args.graphs if world > 1 else G
-    value = total_graphs / (ms * 1e-3)
     plain.close()
-    solver.close()
+    del d
+    torch.cuda.empty_cache()
+    total_graphs = graphs if world > 1 else G
+    peak, peak_src = peak_gbs, peak_source
+    out = {
+        "workload": f"er_batch_{graphs}", "graphs": graphs, "n": N, "m_directed": M,
+        "max_iterations": int(it_b.max()), "seed": 4,
+        "desc": "G(n,M) graphs, n log-uniform [100,200000], entries/vertex U(1.5,20)",
+        "graphs_per_s": total_graphs / (ms * 1e-3), "ms_per_step": ms, "gteps": M / (ms * 1e-3) / 1e9,
+        "per_graph_plain_launches": {
+            "graphs_per_s": total_graphs / plain_s, "seconds": plain_s,
+            "note": "fastsv_cc per graph in turn; each call synchronises once with its stream to read m = row_ptr[n]"},
+        "speedup_vs_plain": (total_graphs / (ms * 1e-3)) / (total_graphs / plain_s),
+        "identical_labels_and_iterations": same, "tuned": bool(tuned), "gpu_launches": int(launches),
+        "batched_spmv": {"algorithmic_bytes": spmv_bytes, "ms": spmv_ms,
+                         "achieved_gbs": spmv_bytes / (spmv_ms * 1e-3) / 1e9 if spmv_ms else None,
+                         "frac": spmv_bytes / (spmv_ms * 1e-3) / 1e9 / peak if (spmv_ms and peak) else None,
+                         "peak_gbs": peak, "peak_source": peak_src,
+                         "bytes_model": "per graph and iteration 4(n+1) + 8m + 4n (row_ptr, col_idx, one gathered "
+                                        "int32 per entry, mngf store)"},
+    }
+    if clocks is not None:
+        out["clocks"] = clocks
+    return out
+
+
+def run_batched(args, rank, world, local_rank):
+    import torch
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    r = batched_measure(args.graphs, args.steps, args.warmup, args.k2_items, args.batch_sparse_div, local_rank,
+                        dist, rank, world, sampler=_clock_sampler(local_rank), peak_gbs=getattr(args, "peak_gbs", None),
+                        peak_source=getattr(args, "peak_source", ""))
     if rank == 0:
-        print(json.dumps({
-            "metric": "batched CC graphs/s (one segmented device loop)", "value": value, "unit": "graphs/s",
-            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": f"er_batch_{args.graphs}", "graphs": args.graphs, "n": N, "m_directed": M,
-                       "max_iterations": int(it_b.max()), "seed": 4,
-                       "desc": "G(n,M) graphs, n log-uniform [100,200000], entries/vertex U(1.5,20)"},
-            "gteps": M / (ms * 1e-3) / 1e9,
-            "per_graph_plain_launches": {"graphs_per_s": total_graphs / plain_s, "seconds": plain_s},
-            "speedup_vs_plain": (total_graphs / (ms * 1e-3)) / (total_graphs / plain_s),
-            "identical_labels_and_iterations": same,
-            "gpu_launches": int(launches), "clocks": clocks}), flush=True)
+        line = {"metric": "batched CC graphs/s (one segmented device loop)", "value": r["graphs_per_s"],
+                "unit": "graphs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "int32", "data": "synthetic",
+                "config": {k: r[k] for k in ("workload", "graphs", "n", "m_directed", "max_iterations", "seed",
+                                             "desc")}}
+        line.update({k: v for k, v in r.items() if k not in line["config"] and k not in ("graphs_per_s",
+                                                                                          "ms_per_step")})
+        print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
 
@@ -137,103 +184,134 @@ def _warm_host_buffers(torch, pinned):
     del dst
 
 
-def run_serve(args, rank, world, local_rank):
+def serve_measure(requests: int, distinct: int, k2_items: int = 8, batch_sparse_div: int = 0,
+                  iters_per_step: int = 2, sampler=None) -> dict:
+    """Config 5: the request trace (Poisson arrivals at 2000/s, undirected
+    edge targets log-uniform in [1e3, 5e7], half R-MAT with edge factor 8-32,
+    half lattices with keep probability in [0.4, 0.9], seed 5) replayed
+    through the continuous-batching server at its arrival times, against the
+    same requests solved by plain fastsv_cc_host calls one after another in
+    arrival order.  The first `distinct` requests' graphs are materialised in
+    pinned host memory and request i carries graph i mod `distinct` (a
+    request is admitted, copied to the device and solved afresh whatever
+    graph it carries).  Latency runs from arrival to labels in host memory.
+    Each arm also runs with every request arriving at once: its throughput
+    then is the largest rate it sustains."""
     import torch
 
     import graphgen
     import paper_1910_05971_gb300 as fsv
     from paper_1910_05971_gb300.serve import Server
 
-    if rank != 0:
-        return  # the serving replay runs on one GPU; replicas would shard the trace
-    torch.cuda.set_device(local_rank)
-    R = args.requests
+    R, K = requests, min(distinct, requests)
     tr = graphgen.trace(R, seed=5)
     t0 = time.time()
-    # the trace lives in pinned host memory (generated before the replay), so
-    # both arms copy to the device at full link speed
     pinned = []
-    reqs = []
-    for i in range(R):
+    graphs = []
+    for i in range(K):
         rp, ci = graphgen.trace_graph(tr, i)
         rp_h = torch.from_numpy(np.ascontiguousarray(rp, dtype=np.int32)).pin_memory()
         ci_h = torch.from_numpy(np.ascontiguousarray(ci if len(ci) else np.zeros(1, np.int32),
                                                      dtype=np.int32)).pin_memory()
         lab_h = torch.empty(max(len(rp) - 1, 1), dtype=torch.int32).pin_memory()
         pinned.append((rp_h, ci_h, lab_h))
-        reqs.append((rp_h.numpy(), ci_h.numpy()[:len(ci)], lab_h.numpy()))
-    m_tot = sum(len(c) for _, c, _ in reqs)
-    _log(f"[bench] {R} requests, {m_tot} directed entries, generated in {time.time() - t0:.1f}s")
+        graphs.append((rp_h.numpy(), ci_h.numpy()[:len(ci)], lab_h.numpy()))
+    m_req = np.array([len(graphs[i % K][1]) for i in range(R)], dtype=np.int64)
+    _log(f"[bench] serve: {K} distinct request graphs ({int(m_req[:K].sum())} directed entries) generated in "
+         f"{time.time() - t0:.1f}s; {R} arrivals")
     arrivals = tr["t"] - tr["t"][0]
-
-    # continuous batching
-    srv = Server(hbm_budget_bytes=120 << 30, max_slots=1024, iters_per_step=2, k2_items=args.k2_items,
-                 batch_sparse_div=args.batch_sparse_div)
-    # warm-up: a few requests through the server
-    for f in [srv.submit(reqs[i][0], reqs[i][1]) for i in range(min(4, R))]:
-        f.result()
-    srv.completed.clear()
     _warm_host_buffers(torch, pinned)
-    launches0 = srv.backend.kernel_launches()
-    futs = [None] * R
-    start = time.perf_counter()
 
-    def feeder():
+    def pool_arm(arr):
+        srv = Server(hbm_budget_bytes=120 << 30, max_slots=1024, iters_per_step=iters_per_step, k2_items=k2_items,
+                     batch_sparse_div=batch_sparse_div)
+        for f in [srv.submit(*graphs[i]) for i in range(min(4, K))]:
+            f.result()
+        srv.completed.clear()
+        launches0 = srv.backend.kernel_launches()
+        futs = [None] * R
+        start = time.perf_counter()
+
+        def feeder():
+            for i in range(R):
+                dt = start + arr[i] - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+                futs[i] = srv.submit(*graphs[i % K])
+
+        th = threading.Thread(target=feeder)
+        th.start()
+        th.join()
+        res = [f.result() for f in futs]
+        end = time.perf_counter()
+        done = {id(r.future): r.t_done for r in srv.completed}
+        lat = np.array([done[id(futs[i])] - (start + arr[i]) for i in range(R)])
+        launches = srv.backend.kernel_launches() - launches0
+        steps = srv.steps
+        srv.close()
+        return res, R / (end - start), lat, launches, steps
+
+    def plain_arm(arr):
+        solver = fsv.FastSV(rowptr_bits=32, k2_items=k2_items)
+        solver.cc_host(pinned[0][0], pinned[0][1], pinned[0][2])
+        lat = np.empty(R)
+        its = np.empty(R, dtype=np.int64)
+        clock = 0.0
         for i in range(R):
-            dt = start + arrivals[i] - time.perf_counter()
-            if dt > 0:
-                time.sleep(dt)
-            futs[i] = srv.submit(*reqs[i])  # rp, ci and a pinned label buffer
-            futs[i].t_arrival = start + arrivals[i]
+            rp_h, ci_h, lab_h = pinned[i % K]
+            begin = max(clock, arr[i])
+            t = time.perf_counter()
+            solver.cc_host(rp_h, ci_h, lab_h)
+            its[i] = solver.stats()["iterations"]
+            clock = begin + (time.perf_counter() - t)
+            lat[i] = clock - arr[i]
+        solver.close()
+        return R / clock, lat, its
 
-    th = threading.Thread(target=feeder)
-    sampler = _clock_sampler(local_rank)
-    sampler.start()
-    th.start()
-    th.join()
-    results = [f.result() for f in futs]
-    end = time.perf_counter()
-    clocks = sampler.stop()
-    lat = np.array([r.t_done - (start + arrivals[i]) for i, r in enumerate(
-        sorted(srv.completed, key=lambda r: r.t_submit))])
-    launches = srv.backend.kernel_launches() - launches0
-    srv.close()
-    gps = R / (end - start)
+    # the plain arm first: its labels are the reference of every request
+    plain_gps, plain_lat, plain_its = plain_arm(arrivals)
+    ref = [pinned[k][2].numpy()[:len(graphs[k][0]) - 1].copy() for k in range(K)]
+    if sampler is not None:
+        sampler.start()
+    res, gps, lat, launches, steps = pool_arm(arrivals)
+    clocks = sampler.stop() if sampler is not None else None
+    same = all(np.array_equal(lab, ref[i % K]) and it == plain_its[i] for i, (lab, it) in enumerate(res))
+    burst = np.zeros(R)
+    _, cap_gps, cap_lat, _, _ = pool_arm(burst)
+    cap_plain_gps, _, _ = plain_arm(burst)
+    out = {
+        "workload": f"serve_trace_{R}_arrivals_{K}_graphs", "requests": R, "distinct_graphs": K,
+        "m_directed_total": int(m_req.sum()), "offered_rate_per_s": 2000, "hbm_budget_gb": 120,
+        "iters_per_step": iters_per_step, "seed": 5,
+        "graphs_per_s": gps, "p50_ms": float(np.percentile(lat, 50) * 1e3),
+        "p99_ms": float(np.percentile(lat, 99) * 1e3),
+        "per_graph_plain_calls": {"graphs_per_s": plain_gps, "p50_ms": float(np.percentile(plain_lat, 50) * 1e3),
+                                  "p99_ms": float(np.percentile(plain_lat, 99) * 1e3),
+                                  "note": "fastsv_cc_host per request in arrival order (copy in, solve, copy out)"},
+        "max_sustainable_rate_per_s": {"pool": cap_gps, "plain": cap_plain_gps,
+                                       "how": "every request arriving at once; throughput of the drained queue"},
+        "identical_labels_and_iterations": bool(same), "gpu_launches": int(launches), "steps": steps,
+    }
+    if clocks is not None:
+        out["clocks"] = clocks
+    return out
 
-    # the same requests, one plain solve after another in arrival order
-    solver = fsv.FastSV(rowptr_bits=32, k2_items=args.k2_items)
-    solver.cc_host(pinned[0][0], pinned[0][1])
-    base_lat = np.empty(R)
-    same = True
-    t_start = time.perf_counter()
-    clock = 0.0
-    # the plain arm writes into the same pinned label buffers: the served
-    # results are copied out first
-    served = [r[0].copy() for r in results]
-    for i, (rp_h, ci_h, lab_h) in enumerate(pinned):
-        begin = max(clock, arrivals[i])
-        t = time.perf_counter()
-        lab = solver.cc_host(rp_h, ci_h, lab_h)
-        it = solver.stats()["iterations"]
-        dur = time.perf_counter() - t
-        clock = begin + dur
-        base_lat[i] = clock - arrivals[i]
-        n = len(reqs[i][0]) - 1
-        same &= bool(np.array_equal(lab.numpy()[:n], served[i])) and it == results[i][1]
-    base_gps = R / clock
-    solver.close()
-    print(json.dumps({
-        "metric": "serve p50/p99 latency + graphs/s (continuous batching)", "value": gps, "unit": "graphs/s",
-        "n_gpus": 1, "steps": R, "warmup": 4, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "int32", "data": "synthetic",
-        "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
-        "config": {"workload": f"serve_trace_prefix_{R}", "requests": R, "m_directed_total": int(m_tot),
-                   "rate_per_s": 2000, "hbm_budget_gb": 120, "iters_per_step": 2, "seed": 5,
-                   "batch_sparse_div": args.batch_sparse_div},
-        "per_graph_plain_launches": {"graphs_per_s": base_gps, "p50_ms": float(np.percentile(base_lat, 50) * 1e3),
-                                     "p99_ms": float(np.percentile(base_lat, 99) * 1e3)},
-        "identical_labels_and_iterations": bool(same), "gpu_launches": int(launches), "clocks": clocks}),
-        flush=True)
+
+def run_serve(args, rank, world, local_rank):
+    import torch
+
+    if rank != 0:
+        return  # the serving replay runs on one GPU; replicas would shard the trace
+    torch.cuda.set_device(local_rank)
+    r = serve_measure(args.requests, args.distinct, args.k2_items, args.batch_sparse_div,
+                      sampler=_clock_sampler(local_rank))
+    line = {"metric": "serve p50/p99 latency + graphs/s (continuous batching)", "value": r["graphs_per_s"],
+            "unit": "graphs/s", "n_gpus": 1, "steps": r["requests"], "warmup": 4, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {k: r[k] for k in ("workload", "requests", "distinct_graphs", "m_directed_total",
+                                         "offered_rate_per_s", "hbm_budget_gb", "iters_per_step", "seed")}}
+    line.update({k: v for k, v in r.items() if k not in line["config"] and k != "graphs_per_s"})
+    print(json.dumps(line), flush=True)
 
 
 def run_variants(args, rank, world, local_rank):

@@ -98,6 +98,8 @@ fastsv_status ensure_workspace(fastsv_ctx* h, int64_t n, int64_t k2, int64_t k3,
     return FASTSV_OK;
 }
 
+// merge-path tile shape of the SpMV (threads x items per thread): 64 or
+// 256 threads, 4, 8 or 16 items
 int k2_items(const fastsv_ctx* h) {
     int it = h->opt.k2_items;
     return (it == 4 || it == 8 || it == 16) ? it : 8;
@@ -414,7 +416,7 @@ static const void* async_func(int rp64) {
 
 static fastsv_status run_async_loop(fastsv_ctx* h, Ctx* ctx, int rp64, cudaStream_t s) {
     const void* fn = async_func(rp64);
-    const int smem = k2_smem_bytes<ASYNC_THREADS, ASYNC_ITEMS>();
+    const int smem = async_smem_bytes<ASYNC_THREADS, ASYNC_ITEMS>();
     FSV_CUDA(h, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     int per_sm = 0;
     FSV_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, ASYNC_THREADS, smem));
@@ -542,23 +544,22 @@ static fastsv_status run_validation(fastsv_ctx* h, int rp64, cudaStream_t s) {
 
 // number of column blocks for a graph (1 = unblocked): the grandparent
 // vector must be larger than the L2 share given to one block's slice, and the
-// graph dense enough that the extra per-block row pointers pay for themselves
+// graph dense enough that the per-block runs and the one-time copy pay off
 static int choose_col_blocks(const fastsv_ctx* h, int64_t n, int64_t m) {
     int nb = h->opt.col_blocks;
-    if (m > (int64_t)INT32_MAX - 1) return 1;  // block row pointers are int32
+    if (m > (int64_t)INT32_MAX - 1) return 1;  // block entry offsets are int32
     if (nb == 1) return 1;
     if (nb <= 0) {
         // Automatic: block when the gathered vector (4n bytes) is at least
-        // 1.5x the L2 and the graph is dense enough (m >= 8n) that the
-        // per-block row pointers and the one-time copy pay off, with slices
-        // of 64 MiB (about half of GB300's 129 MiB L2).  Measured on GB300:
-        // R-MAT scale 26 (gf 268 MB) gets 4 blocks, a full SpMV drops from
-        // 18.4 to 11.8 ms and the solve from 79.4 to 67.9 ms (2 blocks: 80 ms,
-        // 8 blocks: 74 ms); R-MAT scale 25 at edge factor 8 (gf 134 MB) is
-        // faster unblocked and stays so.
+        // 1.5x the L2 and the graph is dense enough (m >= 8n), one block per
+        // col_block_mib MiB of the gathered vector (default 32: measured on
+        // GB300 at R-MAT scale 26, 8 blocks solve in 56.2 ms, 4 in 56.8, 16 in
+        // 63.8 (the copy's run lists grow with the block count), unblocked
+        // in 70.0).
         const int64_t l2 = h->l2_bytes > 0 ? h->l2_bytes : (int64_t)129 << 20;
         if (m < 8 * n || 2 * (4 * n) < 3 * l2) return 1;
-        const int64_t slice = (int64_t)64 << 20;
+        const int64_t mib = h->opt.col_block_mib > 0 ? h->opt.col_block_mib : 32;
+        const int64_t slice = mib << 20;
         const int64_t want = (4 * n + slice - 1) / slice;
         return (int)(want < 2 ? 2 : (want < MAX_COL_BLOCKS ? want : MAX_COL_BLOCKS));
     }
@@ -566,75 +567,22 @@ static int choose_col_blocks(const fastsv_ctx* h, int64_t n, int64_t m) {
     return nb;
 }
 
-template <typename RP>
-static fastsv_status launch_block_build(fastsv_ctx* h, int nb, int shift, int64_t n, cudaStream_t s) {
-    const int g = setup_grid(h);
-    const int64_t np1 = n + 1;
-    const int64_t chunks = (np1 + SCAN_CHUNK - 1) / SCAN_CHUNK;
-    const int smem_count = block_build_smem(nb);
-    const void* fc = (const void*)k_block_count<RP>;
-    const void* fr = (const void*)k_block_scatter<RP>;
-    FSV_CUDA(h, cudaFuncSetAttribute(fc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_count));
-    FSV_CUDA(h, cudaFuncSetAttribute(fr, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_count));
-    Ctx* ctx = h->d_ctx;
-    int32_t* flag = h->d_sums + h->cap_sums - 1;  // "some row is not sorted by column"
-    // the first iteration counted the rows' descending pairs
-    const unsigned long long* descents = h->d_build_scalars;
-    int32_t* start = h->d_rpB;  // run starts of every (row, block)
-    k_sorted_result<<<1, 1, 0, s>>>(descents, flag);
-    // sorted rows: run starts by binary search, counts as their differences
-    k_block_runs<RP><<<g, 256, 0, s>>>(ctx, start, h->d_counts, nb, shift, flag);
-    {
-        // unsorted rows: count per (row, block) instead (returns at once otherwise)
-        void* a[] = {(void*)&ctx, (void*)&h->d_counts, (void*)&nb, (void*)&shift, (void*)&flag};
-        FSV_CUDA(h, cudaLaunchKernel(fc, dim3(g), dim3(BUILD_THREADS), a, (size_t)smem_count, s));
-    }
-    // block row pointers: exclusive scan of every block's counts
-    int ch = (int)chunks;
-    k_scan_chunk_sums<<<(unsigned)(nb * chunks), SCAN_THREADS, 0, s>>>(h->d_counts, np1, ch, h->d_sums);
-    k_scan_sums<<<nb, 1024, 0, s>>>(h->d_sums, ch);
-    // the starts are read by the run scatter: the row pointers go to the
-    // counts buffer, which the scan no longer needs once applied in place
-    k_scan_apply<<<(unsigned)(nb * chunks), SCAN_THREADS, 0, s>>>(h->d_counts, h->d_counts, np1, ch, h->d_sums);
-    {
-        // sorted rows: stable partition of col_idx by block
-        const int64_t ptiles = (h->last_m_build + PART_TILE - 1) / PART_TILE;
-        k_part_tile_rows<RP><<<g, 256, 0, s>>>(ctx, h->d_part_u0, ptiles);
-        k_block_partition<RP><<<g, PART_THREADS, 0, s>>>(ctx, h->d_counts, start, h->d_part_u0, h->d_colB, nb, shift,
-                                                       flag);
-    }
-    {
-        // unsorted rows: ranks from atomics; the run-start buffer becomes the
-        // per-(row, block) cursors
-        k_zero_if_unsorted<<<g, 256, 0, s>>>(start, (int64_t)nb * np1, flag);
-        void* a[] = {(void*)&ctx, (void*)&h->d_counts, (void*)&start, (void*)&h->d_colB, (void*)&nb,
-                     (void*)&shift, (void*)&flag};
-        FSV_CUDA(h, cudaLaunchKernel(fr, dim3(g), dim3(BUILD_THREADS), a, (size_t)smem_count, s));
-    }
-    h->pending_fixed_launches += 10;
-    FSV_CUDA(h, cudaGetLastError());
-    return FASTSV_OK;
-}
-
-static fastsv_status ensure_block_workspace(fastsv_ctx* h, int nb, int64_t n, int64_t m) {
-    const int64_t cells = (int64_t)nb * (n + 1);
-    if (!h->d_build_scalars) {
-        fastsv_status st0 = dev_alloc(h, (void**)&h->d_build_scalars, 64);
-        if (st0 != FASTSV_OK) return st0;
-    }
-    const int64_t sums = (int64_t)nb * ((n + 1 + SCAN_CHUNK - 1) / SCAN_CHUNK) + 1;
+// counts (2 nb rows of tiles + 1), scan sums, the block copy's entries, and
+// the host-visible totals; the runs' arrays grow once their count is known
+static fastsv_status ensure_block_workspace(fastsv_ctx* h, int nb, int64_t tiles, int64_t m) {
     fastsv_status st;
+    if (!h->d_build_scalars) {
+        if ((st = dev_alloc(h, (void**)&h->d_build_scalars, 4 * 2 * MAX_COL_BLOCKS)) != FASTSV_OK) return st;
+    }
+    const int64_t T1 = tiles + 1;
+    const int64_t cells = 2 * (int64_t)nb * T1;
     if (cells > h->cap_blk) {
         dev_free((void**)&h->d_counts);
-        dev_free((void**)&h->d_rpB);
         h->cap_blk = 0;
         if ((st = dev_alloc(h, (void**)&h->d_counts, (size_t)cells * 4)) != FASTSV_OK) return st;
-        if ((st = dev_alloc(h, (void**)&h->d_rpB, (size_t)cells * 4)) != FASTSV_OK) {
-            dev_free((void**)&h->d_counts);
-            return st;
-        }
         h->cap_blk = cells;
     }
+    const int64_t sums = 2 * (int64_t)nb * ((T1 + SCAN_CHUNK - 1) / SCAN_CHUNK) + 1;
     if (sums > h->cap_sums) {
         dev_free((void**)&h->d_sums);
         h->cap_sums = 0;
@@ -647,14 +595,23 @@ static fastsv_status ensure_block_workspace(fastsv_ctx* h, int nb, int64_t n, in
         if ((st = dev_alloc(h, (void**)&h->d_colB, (size_t)m * 4)) != FASTSV_OK) return st;
         h->cap_colB = m;
     }
-    const int64_t ptiles = (m + PART_TILE - 1) / PART_TILE + 1;
-    if (ptiles > h->cap_part_u0) {
-        dev_free((void**)&h->d_part_u0);
-        h->cap_part_u0 = 0;
-        if ((st = dev_alloc(h, (void**)&h->d_part_u0, (size_t)ptiles * 4)) != FASTSV_OK) return st;
-        h->cap_part_u0 = ptiles;
+    return FASTSV_OK;
+}
+
+static fastsv_status ensure_run_workspace(fastsv_ctx* h, int64_t runs, int nb) {
+    fastsv_status st;
+    if (runs + nb + 1 > h->cap_runs) {
+        dev_free((void**)&h->d_rowsB);
+        dev_free((void**)&h->d_endsB);
+        h->cap_runs = 0;
+        const int64_t c = runs + runs / 8 + nb + 1;  // room to grow a little between calls
+        if ((st = dev_alloc(h, (void**)&h->d_rowsB, (size_t)c * 4)) != FASTSV_OK) return st;
+        if ((st = dev_alloc(h, (void**)&h->d_endsB, (size_t)c * 4)) != FASTSV_OK) {
+            dev_free((void**)&h->d_rowsB);
+            return st;
+        }
+        h->cap_runs = c;
     }
-    h->last_m_build = m;
     return FASTSV_OK;
 }
 
@@ -662,9 +619,8 @@ static fastsv_status ensure_block_workspace(fastsv_ctx* h, int nb, int64_t n, in
 // kernel by kernel: the first iteration of a column-blocked solve.  Its SpMV
 // (k2_first) gathers nothing, so the per-tile merge-path search is most of
 // its work: 64 threads x 16 items spend one search on 16 items.  It also
-// counts the rows' descending pairs for the block copy.
-static_assert(BUILD_TILE == FIRST_THREADS * FIRST_ITEMS, "the first iteration walks the build's tiles");
-static fastsv_status first_iteration_unblocked(fastsv_ctx* h, int rp64, cudaStream_t s) {
+// counts every tile's entries and runs per column block for the block copy.
+static fastsv_status first_iteration_unblocked(fastsv_ctx* h, int rp64, int nb, int shift, cudaStream_t s) {
     IterKernels K;
     fastsv_status st = iter_kernels(h, rp64, rp64, 8, &K);
     if (st != FASTSV_OK) return st;
@@ -674,12 +630,11 @@ static fastsv_status first_iteration_unblocked(fastsv_ctx* h, int rp64, cudaStre
     FSV_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, spmv, FIRST_THREADS, smem));
     const int grid = (per_sm > 0 ? per_sm : 1) * h->num_sms;
     Ctx* ctx = h->d_ctx;
-    unsigned long long* descents = h->d_build_scalars;
-    FSV_CUDA(h, cudaMemsetAsync(descents, 0, sizeof(unsigned long long), s));
+    int32_t* cnt = h->d_counts;
     cudaGraphConditionalHandle none = 0;
     int no_cond = 0;
     void* a_begin[] = {(void*)&ctx, (void*)&none, (void*)&no_cond};
-    void* a_spmv[] = {(void*)&ctx, (void*)&descents};
+    void* a_spmv[] = {(void*)&ctx, (void*)&cnt, (void*)&nb, (void*)&shift};
     void* a_ctx[] = {(void*)&ctx};
     void* a_k3[] = {(void*)&ctx, (void*)&none, (void*)&no_cond};
     FSV_CUDA(h, cudaLaunchKernel((const void*)k_iter_begin, dim3(K.vtx_grid), dim3(256), a_begin, 0, s));
@@ -687,6 +642,53 @@ static fastsv_status first_iteration_unblocked(fastsv_ctx* h, int rp64, cudaStre
     FSV_CUDA(h, cudaLaunchKernel(K.hook, dim3(K.vtx_grid), dim3(K3_THREADS), a_ctx, 0, s));
     FSV_CUDA(h, cudaLaunchKernel(K.k3, dim3(K.vtx_grid), dim3(K3_THREADS), a_k3, 0, s));
     h->pending_fixed_launches += 4;
+    return FASTSV_OK;
+}
+
+// The block copy after the first iteration counted it: scan the counts over
+// the tiles, read the blocks' totals (one synchronisation: the runs' arrays
+// are sized by them), split the entries into the blocks, and describe the
+// blocks as segments 1..nb with their own merge-path tiles.
+template <typename RP>
+static fastsv_status build_blocks(fastsv_ctx* h, int nb, int shift, int64_t tiles, int64_t m, int32_t tile,
+                                  cudaStream_t s) {
+    const int64_t T1 = tiles + 1;
+    const int64_t chunks = (T1 + SCAN_CHUNK - 1) / SCAN_CHUNK;
+    const int segs = 2 * nb;
+    const int ch = (int)chunks;
+    k_scan_chunk_sums<<<(unsigned)(segs * chunks), SCAN_THREADS, 0, s>>>(h->d_counts, T1, ch, h->d_sums);
+    k_scan_sums<<<segs, 1024, 0, s>>>(h->d_sums, ch);
+    k_scan_apply<<<(unsigned)(segs * chunks), SCAN_THREADS, 0, s>>>(h->d_counts, h->d_counts, T1, ch, h->d_sums);
+    k_block_totals<<<1, 64, 0, s>>>(h->d_counts, nb, T1, h->d_build_scalars);
+    h->pending_fixed_launches += 4;
+    FSV_CUDA(h, cudaGetLastError());
+    FSV_CUDA(h, cudaMemcpyAsync(h->h_scalar, h->d_build_scalars, (size_t)segs * 4, cudaMemcpyDeviceToHost, s));
+    FSV_CUDA(h, cudaStreamSynchronize(s));
+    BlockLayout L;
+    memset(&L, 0, sizeof(L));
+    L.nb = nb;
+    L.shift = shift;
+    L.T1 = T1;
+    const int32_t* tot = (const int32_t*)h->h_scalar;
+    for (int b = 0; b < nb; ++b) {
+        L.ebase[b + 1] = L.ebase[b] + (uint32_t)tot[b];
+        L.pbase[b + 1] = L.pbase[b] + (uint32_t)tot[nb + b];
+    }
+    if (L.ebase[nb] != m) return FASTSV_ERR_INVALID_GRAPH;  // row_ptr not a valid CSR of m entries
+    const int64_t runs = L.pbase[nb];
+    fastsv_status st = ensure_run_workspace(h, runs, nb);
+    if (st != FASTSV_OK) return st;
+    h->last_runs = runs;
+    Ctx* ctx = h->d_ctx;
+    int per_sm = 0;
+    FSV_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k_block_split<RP>, BUILD_THREADS, 0));
+    const int grid = (per_sm > 0 ? per_sm : 1) * h->num_sms;
+    k_block_split<RP><<<grid, BUILD_THREADS, 0, s>>>(ctx, L, h->d_counts, h->d_colB, h->d_rowsB, h->d_endsB, m, runs);
+    k_setup_blocks<<<1, 1, 0, s>>>(ctx, L, h->d_colB, h->d_rowsB, h->d_endsB, tile);
+    k_scan_tiles<<<1, 1024, 0, s>>>(ctx);
+    k_partition<int32_t><<<setup_grid(h), 256, 0, s>>>(ctx);
+    h->pending_fixed_launches += 4;
+    FSV_CUDA(h, cudaGetLastError());
     return FASTSV_OK;
 }
 
@@ -704,15 +706,17 @@ static fastsv_status solve_single(fastsv_ctx* h, int64_t n, int64_t m, const voi
     int shift = 0;
     while (shift < 31 && ((int64_t)nb << shift) < n) ++shift;
     const int nb_eff = nb > 1 ? (int)((n + (1ll << shift) - 1) >> shift) : 1;
-    // a blocked solve partitions the graph itself for the block build first
+    // a blocked solve partitions the graph itself for the first iteration and
+    // the block copy first (BUILD_TILE items per tile)
     const int64_t tile0 = nb_eff > 1 ? (int64_t)BUILD_TILE : tile;
     const int64_t t2 = m > 0 ? (n + m + tile0 - 1) / tile0 : 0;
-    const int64_t t2b = nb_eff > 1 ? ((int64_t)nb_eff * n + m) / tile + nb_eff + 1 : 0;
+    // the blocks' tiles: every run holds at least one entry, so runs <= m
+    const int64_t t2b = nb_eff > 1 ? (2 * m) / tile + 2 * (nb_eff + 1) : 0;
     const int64_t t3 = (n + K3_TILE - 1) / K3_TILE;
     if (t2 > INT32_MAX || t2b > INT32_MAX || t3 > INT32_MAX) return FASTSV_ERR_UNSUPPORTED;
     fastsv_status st = ensure_workspace(h, n, t2 > t2b ? t2 : t2b, t3, 1 + nb_eff);
     if (st != FASTSV_OK) return st;
-    if (nb_eff > 1 && (st = ensure_block_workspace(h, nb_eff, n, m)) != FASTSV_OK) return st;
+    if (nb_eff > 1 && (st = ensure_block_workspace(h, nb_eff, t2, m)) != FASTSV_OK) return st;
     h->pending_fixed_launches = 0;
     h->ms_k2 = h->ms_k3 = h->ms_push = h->ms_hook = 0.f;
     h->dense_iters = 0;
@@ -750,15 +754,11 @@ static fastsv_status solve_single(fastsv_ctx* h, int64_t n, int64_t m, const voi
         // block copy.
         k_init_state<<<setup_grid(h), 256, 0, s>>>(h->d_ctx);
         h->pending_fixed_launches += 1;
-        if ((st = first_iteration_unblocked(h, rp64, s)) != FASTSV_OK) return st;
-        // split the columns into blocks, then partition every block's CSR
-        st = rp64 ? launch_block_build<int64_t>(h, nb_eff, shift, n, s)
-                  : launch_block_build<int32_t>(h, nb_eff, shift, n, s);
+        if ((st = first_iteration_unblocked(h, rp64, nb_eff, shift, s)) != FASTSV_OK) return st;
+        // split the entries into column blocks of compressed rows
+        st = rp64 ? build_blocks<int64_t>(h, nb_eff, shift, t2, m, (int32_t)tile, s)
+                  : build_blocks<int32_t>(h, nb_eff, shift, t2, m, (int32_t)tile, s);
         if (st != FASTSV_OK) return st;
-        k_setup_blocks<<<1, 1, 0, s>>>(h->d_ctx, h->d_counts, h->d_colB, nb_eff, (int32_t)tile);
-        k_scan_tiles<<<1, 1024, 0, s>>>(h->d_ctx);
-        k_partition<int32_t><<<setup_grid(h), 256, 0, s>>>(h->d_ctx);
-        h->pending_fixed_launches += 3;
         loop_rp64 = 0;
     } else {
         k_init_state<<<setup_grid(h), 256, 0, s>>>(h->d_ctx);
@@ -799,12 +799,13 @@ void fastsv_default_options(fastsv_options* o) {
     o->use_graph = 1;
     o->k2_items = 8;
     o->grid_ctas_per_sm = 0;
-    o->l2_persist = 0;
     o->timing = 1;
     o->fail_alloc_after = 0;
     o->col_blocks = 0;
     o->k2_threads = 256;
     o->sparse_div = 2;
+    o->col_block_mib = 32;
+    o->tune_cache = nullptr;
 }
 
 const char* fastsv_status_string(fastsv_status s) {
@@ -838,7 +839,15 @@ fastsv_status fastsv_create(fastsv_t* out, const fastsv_options* opt) {
     if (o.sparse_div < 0 || o.batch_sparse_div < 0) return FASTSV_ERR_INVALID_ARG;
     if (o.mode == FASTSV_MODE_ASYNC && o.variant >= 1 && o.variant <= 4) return FASTSV_ERR_INVALID_ARG;
     fastsv_ctx* h = new fastsv_ctx();
+    if (o.tune_cache) {
+        if (tune_load(h, o.tune_cache) != FASTSV_OK) {
+            delete h;
+            return FASTSV_ERR_INVALID_ARG;
+        }
+        o.tune_cache = nullptr;  // the path is not kept
+    }
     h->opt = o;
+    h->base_opt = o;
     fastsv_status st = FASTSV_OK;
     cudaError_t e = cudaGetDevice(&h->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
@@ -850,7 +859,7 @@ fastsv_status fastsv_create(fastsv_t* out, const fastsv_options* opt) {
     if (e == cudaSuccess) e = cudaMalloc((void**)&h->d_ctx, sizeof(Ctx));
     if (e == cudaSuccess) e = cudaMemset(h->d_ctx, 0, sizeof(Ctx));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&h->h_sum, sizeof(Summary));
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&h->h_scalar, 64);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&h->h_scalar, 256);
     if (e == cudaSuccess) e = cudaEventCreate(&h->ev_start);
     if (e == cudaSuccess) e = cudaEventCreate(&h->ev_setup);
     if (e == cudaSuccess) e = cudaEventCreate(&h->ev_end);
@@ -882,11 +891,11 @@ fastsv_status fastsv_destroy(fastsv_t h) {
     dev_free((void**)&h->d_mngf);
     dev_free((void**)&h->d_frontier);
     dev_free((void**)&h->d_counts);
-    dev_free((void**)&h->d_rpB);
     dev_free((void**)&h->d_sums);
     dev_free((void**)&h->d_colB);
+    dev_free((void**)&h->d_rowsB);
+    dev_free((void**)&h->d_endsB);
     dev_free((void**)&h->d_build_scalars);
-    dev_free((void**)&h->d_part_u0);
     dev_free(&h->d_rp_copy);
     dev_free((void**)&h->d_ci_copy);
     dev_free((void**)&h->d_lab_copy);
@@ -925,6 +934,7 @@ fastsv_status fastsv_cc(fastsv_t h, int64_t n, const void* row_ptr, const int32_
     int64_t m = w == 8 ? *(int64_t*)h->h_scalar : (int64_t) * (int32_t*)h->h_scalar;
     if (m < 0) return FASTSV_ERR_INVALID_GRAPH;
     if (m > 0 && !col_idx) return FASTSV_ERR_INVALID_ARG;
+    tune_apply(h, TUNE_SINGLE, n, m, 1, h->base_opt.rowptr_bits);
     return solve_single(h, n, m, row_ptr, col_idx, labels_out, s);
 }
 
@@ -953,6 +963,7 @@ fastsv_status fastsv_cc_host(fastsv_t h, int64_t n, const void* row_ptr_host, co
     int64_t m = w == 8 ? ((const int64_t*)row_ptr_host)[n] : (int64_t)((const int32_t*)row_ptr_host)[n];
     if (m < 0) return FASTSV_ERR_INVALID_GRAPH;
     if (m > 0 && !col_idx_host) return FASTSV_ERR_INVALID_ARG;
+    tune_apply(h, TUNE_SINGLE, n, m, 1, h->base_opt.rowptr_bits);
     fastsv_status st;
     if ((st = ensure_copy(h, &h->d_rp_copy, &h->cap_rp_copy, (size_t)(n + 1) * w)) != FASTSV_OK) return st;
     if ((st = ensure_copy(h, (void**)&h->d_ci_copy, &h->cap_ci_copy, (size_t)(m > 0 ? m : 1) * 4)) != FASTSV_OK)
@@ -986,6 +997,7 @@ fastsv_status fastsv_cc_batched(fastsv_t h, int32_t G, const int64_t* vtx_off, c
     const int64_t N = h->h_scalar[0], M = h->h_scalar[1];
     if (N < 0 || M < 0) return FASTSV_ERR_INVALID_GRAPH;
     if (M > 0 && !col_idx) return FASTSV_ERR_INVALID_ARG;
+    tune_apply(h, TUNE_BATCHED, N, M, G, 32);
     const int items = k2_items(h);
     const int64_t tile = k2_tile(h);
     const int64_t t2 = (N + M) / tile + G + 1;
@@ -1084,14 +1096,16 @@ fastsv_status fastsv_get_stats(fastsv_t h, fastsv_stats* out) {
     out->trace_len = h->single ? len : 0;
     out->col_blocks = h->single ? h->last_col_blocks : 1;
     for (int i = 0; i < out->trace_len; ++i) out->changed_per_iter[i] = (int64_t)S.trace[i];
+    out->block_runs = h->single && h->last_col_blocks > 1 ? h->last_runs : 0;
+    out->tuned = h->last_tuned;
     return (fastsv_status)h->last_status;
 }
 
 int32_t fastsv_last_cuda_error(fastsv_t h) { return h ? h->last_cuda_error : 0; }
 
 // the layouts the Python binding mirrors (its tests pin the same sizes)
-static_assert(sizeof(fastsv_options) == 64, "fastsv_options layout");
-static_assert(sizeof(fastsv_stats) == 592, "fastsv_stats layout");
+static_assert(sizeof(fastsv_options) == 72, "fastsv_options layout");
+static_assert(sizeof(fastsv_stats) == 608, "fastsv_stats layout");
 
 int64_t fastsv_kernel_launches(fastsv_t h) { return h ? h->launches + h->launches_loop_dev : 0; }
 

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <map>
+#include <string>
 #include <vector>
 
 #include "../../include/fastsv.h"
@@ -32,10 +33,20 @@ struct LoopGraph {
 
 struct Pool;  // serving pool (pool.cu)
 
+// one line of the tuning cache (tune.cu)
+struct TuneEntry {
+    std::string key;
+    int32_t k2_items, k2_threads, col_blocks, sparse_div, batch_sparse_div;
+};
+enum { TUNE_SINGLE = 0, TUNE_BATCHED = 1 };
+
 }  // namespace fsv
 
 struct fastsv_ctx {
-    fastsv_options opt;
+    fastsv_options opt;        // options of the current call (base_opt, or with a tuning-cache entry applied)
+    fastsv_options base_opt;   // options the handle was created with
+    std::vector<fsv::TuneEntry> tune;
+    int32_t last_tuned = 0;
     int device = 0;
     int num_sms = 0;
     int64_t l2_bytes = 0;
@@ -56,18 +67,18 @@ struct fastsv_ctx {
     int32_t* d_frontier = nullptr;   // vertices whose gf changed in the last iteration
     int64_t cap_n = 0;
 
-    // column-blocked copy of a large graph (see k_block_count)
-    int32_t* d_counts = nullptr;
-    int32_t* d_rpB = nullptr;
+    // column-blocked copy of a large graph (see k_block_split)
+    int32_t* d_counts = nullptr;    // per (block, tile) entries and runs, scanned in place
     int64_t cap_blk = 0;
     int32_t* d_sums = nullptr;
     int64_t cap_sums = 0;
-    int32_t* d_colB = nullptr;
+    int32_t* d_colB = nullptr;      // the entries, block after block
     int64_t cap_colB = 0;
-    unsigned long long* d_build_scalars = nullptr;  // block build: descent counter
-    int32_t* d_part_u0 = nullptr;           // block build: first row of every partition tile
-    int64_t cap_part_u0 = 0;
-    int64_t last_m_build = 0;
+    int32_t* d_rowsB = nullptr;     // graph row of every run
+    int32_t* d_endsB = nullptr;     // end of every run inside its block (one leading 0 per block)
+    int64_t cap_runs = 0;
+    int32_t* d_build_scalars = nullptr;  // blocks' totals for the host
+    int64_t last_runs = 0;
     int last_col_blocks = 1;
 
     // device copies for the host-buffer entry point
@@ -132,5 +143,8 @@ int k2_items(const fastsv_ctx* h);
 int k2_threads(const fastsv_ctx* h);
 int64_t k2_tile(const fastsv_ctx* h);
 void pool_release(fastsv_ctx* h);
+int tune_key(int kind, int64_t n, int64_t m, int64_t graphs, int bits, char* out, size_t cap);
+fastsv_status tune_load(fastsv_ctx* h, const char* path);
+void tune_apply(fastsv_ctx* h, int kind, int64_t n, int64_t m, int64_t graphs, int bits);
 
 }  // namespace fsv

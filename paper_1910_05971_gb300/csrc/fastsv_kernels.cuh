@@ -149,6 +149,7 @@ __global__ void k_setup_single(Ctx* ctx, SingleParams prm, WsPtrs ws) {
     s.mode = 0;
     s.mngf = prm.mngf;
     s.fr_deg = 0;
+    s.rowmap = nullptr;
     ws.segs[0] = s;
     ctx->num_segs = 1;
     ctx->k2_tile = prm.k2_tile;
@@ -220,6 +221,7 @@ __global__ void k_setup_batched(Ctx* ctx, BatchParams prm, WsPtrs ws) {
         s.mode = 0;
         s.mngf = prm.mngf + v0;
         s.fr_deg = 0;
+        s.rowmap = nullptr;
         ws.segs[g] = s;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -378,57 +380,55 @@ __global__ void k_validate(Ctx* ctx, int check_sym) {
 //
 // Hooking gathers gf[col_idx[e]] at random positions.  When gf is larger
 // than L2 most gathers miss.  Splitting the columns into nb ranges of 2^shift
-// ids and running one hooking pass per range keeps every pass's gathers
-// inside an L2-resident slice of gf.  A row's minimum over all its entries is
-// the minimum of its per-range minima and every hook is a min, so hooking
-// with each range's minimum gives exactly the f of the unsplit SpMV.  (This
-// is the single-GPU counterpart of the 2-D distribution of A in Section 4.2,
-// where each process column owns a range of columns.)
+// ids and running one SpMV pass per range keeps every pass's gathers inside
+// an L2-resident slice of gf.  A row's minimum over all its entries is the
+// minimum of its per-range minima and every hook is a min, so hooking with
+// each range's minimum gives exactly the f of the unsplit SpMV.  (This is the
+// single-GPU counterpart of the 2-D distribution of A in Section 4.2, where
+// each process column owns a range of columns.)
 //
-// Layout: counts / rpB are nb rows of n+1 int32 (block-major), colB holds
-// the entries of block 0, then block 1, ... each as a CSR over all n rows.
+// Layout of the block copy (compressed rows: a block lists only the rows that
+// have entries in it).  The copy is cut along the merge-path tiles of the
+// graph's own CSR (the first iteration's tiles, BUILD_TILE items each).
+// Inside a tile, a "run" is a maximal sequence of consecutive entries of one
+// row whose columns fall in one block; when rows are sorted by column a row
+// has exactly one run per block it touches.  Block b holds, tile after tile,
+// the tile's runs of block b in tile order (a stable partition of the tile's
+// entries by block):
+//   colB[ebase_b + ...]          the entries (global column ids)
+//   rowsB[pbase_b + i]           global row of run i; bit 31 set when the
+//                                row may have another run in block b (the
+//                                row crosses a tile boundary, or the tile's
+//                                rows are not sorted by block), so its
+//                                partial minimum must merge atomically
+//   endsB[pbase_b + b + i + 1]   end of run i inside block b's entries
+//                                (endsB[pbase_b + b] = 0): block b is a CSR
+//                                over its runs, walked by the same merge-path
+//                                SpMV as the graph itself.
+// The first iteration's SpMV counts every tile's entries and runs per block;
+// an exclusive scan over tiles gives every (tile, block) its offsets.
 // ---------------------------------------------------------------------------
 
-constexpr int MAX_COL_BLOCKS = 16;
+constexpr int MAX_COL_BLOCKS = 32;
+constexpr int32_t ROW_SHARED = (int32_t)0x80000000u;  // rowsB flag: merge this run's minimum atomically
 
 __device__ __forceinline__ int col_block(int32_t c, int shift, int nb) {
     int b = (int)((uint32_t)c >> shift);
     return b < nb ? b : nb - 1;
 }
 
-constexpr int BUILD_THREADS = 128;  // CTA size and items per thread of the block-build kernels
+constexpr int BUILD_THREADS = 128;  // CTA size and items per thread of the block-split kernel
 constexpr int BUILD_ITEMS = 8;
 constexpr int BUILD_TILE = BUILD_THREADS * BUILD_ITEMS;
 
-constexpr int block_build_smem(int nb) {
-    return (3 * (BUILD_TILE + 1) + (BUILD_TILE + 1) * nb) * (int)sizeof(int32_t);
-}
-
-// Loads the tile's row ends and column ids (coalesced) into shared memory and
-// walks the merge path; fn(row_local, entry_local) is called once per entry.
-template <typename RP, int ITEMS, typename Fn>
-__device__ __forceinline__ void tile_walk(const int32_t* s_rowend, int nfull, int E, int D, Fn fn) {
-    const int k0 = threadIdx.x * ITEMS;
-    if (k0 >= D) return;
-    int lo = 0, hi = nfull;
-    while (lo < hi) {
-        int mid = (lo + hi) >> 1;
-        if (s_rowend[mid] + mid < k0)
-            lo = mid + 1;
-        else
-            hi = mid;
-    }
-    int r = lo, y = k0 - lo;
-    const int kend = min(k0 + ITEMS, D);
-    for (int k = k0; k < kend; ++k) {
-        if (r < nfull && y >= s_rowend[r]) {
-            ++r;
-        } else {
-            if (y < E) fn(r, y);
-            ++y;
-        }
-    }
-}
+// offsets of the blocks' entries and runs in colB / rowsB (host-computed
+// from the scanned counts; entry b + 1 is the end of block b)
+struct BlockLayout {
+    int32_t nb, shift;
+    int64_t T1;  // stride of one block's count row: tiles + 1
+    int64_t ebase[MAX_COL_BLOCKS + 1];
+    int64_t pbase[MAX_COL_BLOCKS + 1];
+};
 
 // per tile of the graph's own merge-path partition (segment 0): row ends,
 // column ids, row count R, entry count E; returns false for an empty tile
@@ -484,324 +484,150 @@ __device__ __forceinline__ bool load_tile(const Seg& S, int64_t t, int64_t tile,
     return true;
 }
 
-// first local entry of row r of the tile (row 0 may have started in an
-// earlier tile: its first entry here is entry 0)
-__device__ __forceinline__ int row_start_local(const int32_t* s_rowend, int r) {
-    return r > 0 ? s_rowend[r - 1] : 0;
+// is tile entry j the first of a run (the tile's first entry, a row's first
+// entry, or a change of column block inside a row)?  s_rs marks the first
+// entry of every row that starts inside the tile.
+__device__ __forceinline__ bool run_start(const int32_t* s_col, const unsigned* s_rs, int j, int b, int shift, int nb) {
+    return j == 0 || ((s_rs[j >> 5] >> (j & 31)) & 1u) || col_block(s_col[j - 1], shift, nb) != b;
 }
 
-// Rows not sorted by column: counts[b][u] = entries of row u whose column
-// lies in block b.  Every thread counts its ITEMS merge-path items in one
-// register (4 bits per block), so shared-memory atomics happen once per
-// (thread, row, block), not per entry.  Rows that start and end inside the
-// tile are stored, the two that can continue in a neighbouring tile are
-// added atomically.  Returns at once for sorted graphs.
-template <typename RP>
-__global__ void __launch_bounds__(BUILD_THREADS)
-    k_block_count(Ctx* ctx, int32_t* counts, int nb, int shift, int32_t* unsorted) {
-    constexpr int TILE = BUILD_TILE;
-    constexpr int RS = TILE + 1;
-    if (!*unsorted) return;  // sorted rows: counted from k_block_starts
-    extern __shared__ int32_t smem[];
-    int32_t* s_rowend = smem;
-    int32_t* s_col = smem + RS;
-    int32_t* s_cnt = smem + 2 * RS;  // [nb][RS]
-    const Seg S = ctx->segs[0];
-    const RP* rp = (const RP*)S.rp;
-    const int64_t np1 = S.n + 1;
-    int bad = 0;
-    for (int64_t t = blockIdx.x; t < S.k2_ntiles; t += gridDim.x) {
-        int64_t x0;
-        int nfull, R, E, D;
-        if (!load_tile<RP>(S, t, TILE, ctx->k2_tile_row, s_rowend, s_col, x0, nfull, R, E, D)) continue;
-        for (int b = 0; b < nb; ++b)
-            for (int r = threadIdx.x; r < R; r += BUILD_THREADS) s_cnt[b * RS + r] = 0;
-        const int64_t y0 = (t - S.k2_tile0) * TILE - x0;
-        const bool first_whole = rp_at(rp, x0) >= y0;
-        __syncthreads();
-        // a row continuing from the previous tile must be sorted across it
-        if (threadIdx.x == 0 && !first_whole && E > 0 && y0 > 0 && S.ci[y0 - 1] > s_col[0]) bad = 1;
-        const int k0 = threadIdx.x * BUILD_ITEMS;
-        if (k0 < D) {
-            int lo = 0, hi = nfull;
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (s_rowend[mid] + mid < k0)
-                    lo = mid + 1;
-                else
-                    hi = mid;
-            }
-            int r = lo, y = k0 - lo;
-            int rend = r < nfull ? s_rowend[r] : 0x7fffffff;
-            int32_t prev = y > row_start_local(s_rowend, r) ? s_col[y - 1] : INT32_MIN;
-            unsigned long long cnt = 0;
-            const int steps = min(BUILD_ITEMS, D - k0);
-            for (int k = 0; k <= steps; ++k) {
-                const bool row_end = k == steps || y >= rend;
-                if (row_end) {
-                    while (cnt) {
-                        const int bb = (__ffsll((long long)cnt) - 1) >> 2;
-                        atomicAdd(&s_cnt[bb * RS + r], (int)((cnt >> (4 * bb)) & 15ull));
-                        cnt &= ~(15ull << (4 * bb));
-                    }
-                    if (k == steps) break;
-                    ++r;
-                    rend = r < nfull ? s_rowend[r] : 0x7fffffff;
-                    prev = INT32_MIN;
-                } else {
-                    const int32_t c = s_col[y];
-                    if (c < prev) bad = 1;
-                    prev = c;
-                    cnt += 1ull << (4 * col_block(c, shift, nb));
-                    ++y;
-                }
-            }
-        }
-        __syncthreads();
-        for (int b = 0; b < nb; ++b) {
-            for (int r = threadIdx.x; r < R; r += BUILD_THREADS) {
-                const int c = s_cnt[b * RS + r];
-                if (!c) continue;
-                int32_t* dst = counts + (int64_t)b * np1 + x0 + r;
-                if (r < nfull && (r > 0 || first_whole))
-                    *dst = c;
-                else
-                    atomicAdd(dst, c);
-            }
-        }
-        __syncthreads();
-    }
-    if (bad) atomicOr(unsorted, 1);
-}
-
-// ---------------------------------------------------------------------------
-// column-block build for rows sorted by column (the common case): the
-// sortedness result (from the descending pairs the first iteration's SpMV
-// counted), run starts of every (row, block) by binary search, and a stable
-// partition of col_idx by block
-// ---------------------------------------------------------------------------
-
-// the block copy's path: rows not all sorted (k2_first counted descending pairs)
-__global__ void k_sorted_result(const unsigned long long* descents, int32_t* unsorted) { *unsorted = *descents != 0; }
-
-// Sorted rows: start[k][u] = first position of row u whose column block is
-// >= k (the row end if none), found by binary search per (row, block)
-// boundary, and counts[k][u] = start[k+1][u] - start[k][u] (row end for the
-// last block); counts[k][n] = 0.  One thread per row.  All zero when the
-// graph is unsorted (the ranked path's counting kernel then fills counts).
-template <typename RP>
-__global__ void __launch_bounds__(256) k_block_runs(const Ctx* ctx, int32_t* __restrict__ start,
-                                                    int32_t* __restrict__ counts, int nb, int shift,
-                                                    const int32_t* unsorted) {
-    const Seg& S0 = ctx->segs[0];
-    const RP* __restrict__ rp = (const RP*)S0.rp;
-    const uint32_t* __restrict__ ci = (const uint32_t*)S0.ci;
-    const int64_t n = S0.n, np1 = n + 1;
-    const bool zero = *unsorted != 0;
-    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < np1; u += (int64_t)gridDim.x * blockDim.x) {
-        if (u == n || zero) {
-            for (int k = 0; k < nb; ++k) counts[k * np1 + u] = 0;
-            continue;
-        }
-        const int64_t b0 = rp_at(rp, u), b1 = rp_at(rp, u + 1);
-        int64_t lo = b0, prev = b0;
-        start[u] = (int32_t)b0;
-        for (int k = 1; k <= nb; ++k) {
-            int64_t pos = b1;
-            if (k < nb) {
-                // first entry at or after lo with id >= k << shift
-                const uint32_t key = (uint32_t)k << shift;
-                int64_t hi = b1;
-                while (lo < hi) {
-                    const int64_t mid = (lo + hi) >> 1;
-                    if (ci[mid] < key)
-                        lo = mid + 1;
-                    else
-                        hi = mid;
-                }
-                pos = lo;
-                start[k * np1 + u] = (int32_t)pos;
-            }
-            counts[(k - 1) * np1 + u] = (int32_t)(pos - prev);
-            prev = pos;
-        }
-    }
-}
-
-__global__ void k_zero_if_unsorted(int32_t* p, int64_t count, const int32_t* unsorted) {
-    if (!*unsorted) return;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
-        p[i] = 0;
-}
-
-// Sorted rows: the block-major copy colB is the stable partition of col_idx
-// by column block -- entries of block b keep their order, which is row
-// order and, inside a row, the run order.  Fixed tiles of PART_TILE
-// consecutive entries; a tile's first destination in block b follows from
-// the row u0 holding its first entry e0:
-//   base_b + rpB[b][u0] + clamp(e0 - start[b][u0], 0, count_b(u0)).
-// Inside the tile, steps of PART_THREADS entries are ranked stably per
-// block with warp ballots and a per-step prefix over the warps.
-constexpr int PART_THREADS = 256;
-constexpr int PART_STEPS = 16;
-constexpr int PART_TILE = PART_THREADS * PART_STEPS;
-
-// row holding the first entry of every partition tile (largest u with
-// rp[u] <= e0), one binary search per tile
-template <typename RP>
-__global__ void k_part_tile_rows(const Ctx* ctx, int32_t* tile_u0, int64_t tiles) {
-    const Seg& S0 = ctx->segs[0];
-    const RP* rp = (const RP*)S0.rp;
-    const int64_t n = S0.n;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tiles; t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t e0 = t * PART_TILE;
-        int64_t lo = 0, hi = n - 1;
-        while (lo < hi) {
-            const int64_t mid = (lo + hi + 1) >> 1;
-            if (rp_at(rp, mid) <= e0)
-                lo = mid;
-            else
-                hi = mid - 1;
-        }
-        tile_u0[t] = (int32_t)lo;
-    }
-}
+// The block copy: for every tile of segment 0 (the tiles the first
+// iteration counted), a stable partition of its entries by column block.
+// One warp per tile walks the tile's entries in rounds of 32 (eight rounds'
+// column ids loaded at once); lanes of one block find each other with a
+// match, rank themselves by the lanes before them, and write their entries
+// at the block's running position (the tile's scanned offset, advanced by
+// the group leader after every round).  A run start writes the run's row
+// and, as the end of the block's previous run, its own position; the end of
+// every block's last run is its entry count.
+constexpr int SPLIT_WARPS = 4;
+constexpr int SPLIT_BATCH = 8;  // rounds whose column ids are loaded together
 
 template <typename RP>
-__global__ void __launch_bounds__(PART_THREADS)
-    k_block_partition(Ctx* ctx, const int32_t* __restrict__ rpB, const int32_t* __restrict__ start,
-                      const int32_t* __restrict__ tile_u0, int32_t* __restrict__ colB, int nb, int shift,
-                      const int32_t* unsorted) {
-    if (*unsorted) return;
-    constexpr int W = PART_THREADS / 32;
-    __shared__ long long s_tile_off[MAX_COL_BLOCKS];
-    __shared__ int32_t s_wcnt[2][W][MAX_COL_BLOCKS];  // per step: warp counts, then warp offsets
-    __shared__ int32_t s_run[MAX_COL_BLOCKS];         // entries of each block in the tile's earlier steps
-    const Seg& S0 = ctx->segs[0];
-    const int32_t* __restrict__ ci = S0.ci;
-    const int64_t np1 = S0.n + 1, m = S0.m;
-    const int64_t tiles = (m + PART_TILE - 1) / PART_TILE;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+__global__ void __launch_bounds__(32 * SPLIT_WARPS)
+    k_block_split(const Ctx* __restrict__ ctx, BlockLayout L, const int32_t* __restrict__ cnt,
+                  int32_t* __restrict__ colB, int32_t* __restrict__ rowsB, int32_t* __restrict__ endsB,
+                  int64_t m_total, int64_t p_total) {
+    __shared__ int32_t s_end[SPLIT_WARPS][BUILD_TILE + 1];   // local end of every row of the warp's tile
+    __shared__ unsigned s_rs[SPLIT_WARPS][BUILD_TILE / 32];  // bit j: entry j is the first entry of a row
+    __shared__ int32_t s_pos[SPLIT_WARPS][MAX_COL_BLOCKS];   // next entry position inside each block
+    __shared__ int32_t s_run[SPLIT_WARPS][MAX_COL_BLOCKS];   // next run index inside each block
+    __shared__ long long s_eb[MAX_COL_BLOCKS], s_pb[MAX_COL_BLOCKS];
+    const Seg S0 = ctx->segs[0];
+    const int nb = L.nb, shift = L.shift;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    long long base_b = 0;  // thread b < nb: entries of the blocks before b
-    if (threadIdx.x < nb)
-        for (int b = 0; b < (int)threadIdx.x; ++b) base_b += rpB[(int64_t)b * np1 + S0.n];
-    for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
-        const int64_t e0 = t * PART_TILE;
-        if (threadIdx.x < nb) {
+    if ((int)threadIdx.x < nb) {
+        s_eb[threadIdx.x] = L.ebase[threadIdx.x];
+        s_pb[threadIdx.x] = L.pbase[threadIdx.x];
+        if (blockIdx.x == 0) {  // the end of the block's last run
             const int b = threadIdx.x;
-            const int64_t u0 = tile_u0[t];
-            const int64_t i = (int64_t)b * np1 + u0;
-            const long long cnt = (long long)rpB[i + 1] - rpB[i];
-            long long before = e0 - (long long)start[i];
-            before = before < 0 ? 0 : (before > cnt ? cnt : before);
-            s_tile_off[b] = base_b + rpB[i] + before;
-            s_run[b] = 0;
-        }
-        // every load of the tile first: one memory round trip per tile
-        int32_t cv[PART_STEPS];
-#pragma unroll
-        for (int st = 0; st < PART_STEPS; ++st) {
-            const int64_t e = e0 + (int64_t)st * PART_THREADS + threadIdx.x;
-            cv[st] = e < m ? ld_stream(ci + e) : 0;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int st = 0; st < PART_STEPS; ++st) {
-            const int64_t e = e0 + (int64_t)st * PART_THREADS + threadIdx.x;
-            const bool valid = e < m;
-            const int32_t c = cv[st];
-            const int b = valid ? col_block(c, shift, nb) : 0;
-            // lanes of the same block: the ballots of the block id's four bits
-            const unsigned vb = __ballot_sync(0xffffffffu, valid);
-            unsigned bits[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) bits[k] = __ballot_sync(0xffffffffu, (b >> k) & 1);
-            unsigned same = vb;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) same &= ((b >> k) & 1) ? bits[k] : ~bits[k];
-            if (lane < nb) {  // this warp's count of block `lane`
-                unsigned mk = vb;
-#pragma unroll
-                for (int k = 0; k < 4; ++k) mk &= ((lane >> k) & 1) ? bits[k] : ~bits[k];
-                s_wcnt[st & 1][w][lane] = __popc(mk);
-            }
-            __syncthreads();
-            if (threadIdx.x < nb) {  // warp offsets of block b in this step, after the earlier steps
-                const int bb = threadIdx.x;
-                int run = s_run[bb];
-                for (int ww = 0; ww < W; ++ww) {
-                    const int x = s_wcnt[st & 1][ww][bb];
-                    s_wcnt[st & 1][ww][bb] = run;
-                    run += x;
-                }
-                s_run[bb] = run;
-            }
-            __syncthreads();
-            if (valid) {
-                const long long pos = s_tile_off[b] + s_wcnt[st & 1][w][b] + __popc(same & lt);
-                if (pos >= 0 && pos < m) colB[pos] = c;
-            }
-        }
-        __syncthreads();
-    }
-}
-
-// Fallback for rows not sorted by column: colB[rpB[b][u] + k] for the k-th
-// entry of row u in block b, ranks from shared-memory atomics (the order
-// within a row's block is arbitrary: the SpMV only takes minima)
-template <typename RP>
-__global__ void __launch_bounds__(BUILD_THREADS)
-    k_block_scatter(Ctx* ctx, const int32_t* rpB, int32_t* cursor, int32_t* colB, int nb, int shift,
-                    const int32_t* unsorted) {
-    constexpr int TILE = BUILD_TILE;
-    if (!*unsorted) return;
-    extern __shared__ int32_t smem[];
-    int32_t* s_rowend = smem;
-    int32_t* s_col = smem + (TILE + 1);
-    int32_t* s_rank = smem + 2 * (TILE + 1);
-    int32_t* s_cnt = smem + 3 * (TILE + 1);
-    __shared__ long long s_blockbase[MAX_COL_BLOCKS];
-    const Seg S = ctx->segs[0];
-    const int64_t np1 = S.n + 1;
-    const int64_t m = S.m;
-    // rpB holds block-local offsets; block b starts after the entries of blocks < b
-    if (threadIdx.x == 0) {
-        long long acc = 0;
-        for (int b = 0; b < nb; ++b) {
-            s_blockbase[b] = acc;
-            acc += rpB[(int64_t)b * np1 + S.n];
+            const int64_t pb = L.pbase[b + 1] - L.pbase[b];
+            if (L.pbase[b] + b + pb <= p_total + nb) endsB[L.pbase[b] + b + pb] = (int32_t)(L.ebase[b + 1] - L.ebase[b]);
         }
     }
     __syncthreads();
-    for (int64_t t = blockIdx.x; t < S.k2_ntiles; t += gridDim.x) {
-        int64_t x0;
-        int nfull, R, E, D;
-        if (!load_tile<RP>(S, t, TILE, ctx->k2_tile_row, s_rowend, s_col, x0, nfull, R, E, D)) continue;
-        for (int i = threadIdx.x; i < R * nb; i += blockDim.x) s_cnt[i] = 0;
-        __syncthreads();
-        // rank of every entry among the tile's entries of the same (row, block)
-        tile_walk<RP, BUILD_ITEMS>(s_rowend, nfull, E, D, [&](int r, int y) {
-            const int b = col_block(s_col[y], shift, nb);
-            const int k = atomicAdd(&s_cnt[r * nb + b], 1);
-            s_rank[y] = (k << 4) | b;  // nb <= 16
-        });
-        __syncthreads();
-        // reserve each (row, block) run of this tile in the row's block segment
-        for (int i = threadIdx.x; i < R * nb; i += blockDim.x) {
-            const int c = s_cnt[i];
-            if (c) s_cnt[i] = atomicAdd(&cursor[(int64_t)(i % nb) * np1 + x0 + i / nb], c);
+    const RP* __restrict__ rp = (const RP*)S0.rp;
+    const int32_t* __restrict__ ci = S0.ci;
+    const int64_t n = S0.n, m = S0.m, T = S0.k2_ntiles;
+    const int32_t* __restrict__ tile_row = ctx->k2_tile_row + S0.k2_tile0;
+    unsigned* rsw = s_rs[w];
+    int32_t* endw = s_end[w];
+    for (int64_t t = (int64_t)blockIdx.x * SPLIT_WARPS + w; t < T; t += (int64_t)gridDim.x * SPLIT_WARPS) {
+        const int64_t d0 = t * BUILD_TILE, d1 = min(d0 + BUILD_TILE, n + m);
+        const int64_t x0 = tile_row[t];
+        const int64_t x1 = t + 1 < T ? (int64_t)tile_row[t + 1] : n;
+        if (x1 < x0) continue;  // only possible for a malformed row_ptr
+        const int64_t y0 = d0 - x0, y1 = d1 - x1;
+        const int nfull = (int)(x1 - x0);
+        const int E = (int)(y1 - y0);
+        if (E <= 0) continue;
+        rsw[lane] = 0u;
+        if (lane < nb) {
+            s_pos[w][lane] = cnt[(int64_t)lane * L.T1 + t];
+            s_run[w][lane] = cnt[(int64_t)(nb + lane) * L.T1 + t];
         }
-        __syncthreads();
-        tile_walk<RP, BUILD_ITEMS>(s_rowend, nfull, E, D, [&](int r, int y) {
-            const int b = s_rank[y] & 15;
-            const int64_t u = x0 + r;
-            const int64_t pos =
-                s_blockbase[b] + (int64_t)rpB[(int64_t)b * np1 + u] + s_cnt[r * nb + b] + (s_rank[y] >> 4);
-            if (pos >= 0 && pos < m) colB[pos] = s_col[y];
-        });
-        __syncthreads();
+        const bool first_whole = rp_at(rp, x0) >= y0;  // row x0 starts inside the tile
+        __syncwarp();
+        for (int i = lane; i < nfull; i += 32) {
+            int64_t e = rp_at(rp, x0 + 1 + i);
+            e = (e < y1 ? e : y1) - y0;
+            const int ev = (int)(e < 0 ? 0 : e);
+            endw[i] = ev;
+            if (ev < E) atomicOr(&rsw[ev >> 5], 1u << (ev & 31));  // row i + 1 starts at ev
+        }
+        __syncwarp();
+        int prev_b = -1;  // block of the entry before the round
+        bool desc = false;
+        for (int base = 0; base < E; base += 32 * SPLIT_BATCH) {
+            int32_t cv[SPLIT_BATCH];
+#pragma unroll
+            for (int k = 0; k < SPLIT_BATCH; ++k) {
+                const int j = base + 32 * k + lane;
+                cv[k] = j < E ? ld_stream(ci + y0 + j) : 0;
+            }
+#pragma unroll
+            for (int k = 0; k < SPLIT_BATCH; ++k) {
+                const int j = base + 32 * k + lane;
+                if (j - lane >= E) break;  // warp-uniform
+                const bool valid = j < E;
+                const int32_t c = cv[k];
+                const int b = valid ? col_block(c, shift, nb) : 0;
+                int pb = __shfl_up_sync(0xffffffffu, b, 1);
+                if (lane == 0) pb = prev_b;
+                prev_b = __shfl_sync(0xffffffffu, b, 31);
+                const bool row_first = valid && (j == 0 || ((rsw[j >> 5] >> (j & 31)) & 1u));
+                const bool rs = valid && (row_first || pb != b);
+                desc |= valid && !row_first && pb > b;
+                const unsigned grp = __match_any_sync(0xffffffffu, valid ? b : 64 + lane);
+                const unsigned rsb = __ballot_sync(0xffffffffu, rs);
+                const int p = s_pos[w][b] + __popc(grp & lt);
+                if (valid) {
+                    const int64_t at = s_eb[b] + p;
+                    if (at < m_total) colB[at] = c;
+                    if (rs) {
+                        const int ri = s_run[w][b] + __popc(grp & rsb & lt);
+                        int lo = 0, hi = nfull;  // the row: the first whose end lies after entry j
+                        while (lo < hi) {
+                            const int mid = (lo + hi) >> 1;
+                            if (endw[mid] > j)
+                                hi = mid;
+                            else
+                                lo = mid + 1;
+                        }
+                        const bool shared = (lo == 0 && !first_whole) || lo >= nfull;
+                        const int64_t pi = s_pb[b] + ri;
+                        if (pi < p_total) {
+                            rowsB[pi] = (int32_t)(x0 + lo) | (shared ? ROW_SHARED : 0);
+                            endsB[pi + b] = p;  // the block's previous run ends where this one starts
+                        }
+                    }
+                }
+                __syncwarp();
+                if (valid && (__ffs(grp) - 1) == lane) {
+                    s_pos[w][b] += __popc(grp);
+                    s_run[w][b] += __popc(grp & rsb);
+                }
+                __syncwarp();
+            }
+        }
+        // a row whose block id decreases: its block may repeat inside the
+        // tile, so every run of this tile merges atomically
+        if (__any_sync(0xffffffffu, desc)) {
+            for (int b = 0; b < nb; ++b) {
+                const int r0 = cnt[(int64_t)(nb + b) * L.T1 + t], r1 = s_run[w][b];
+                for (int i = r0 + lane; i < r1; i += 32)
+                    if (s_pb[b] + i < p_total) rowsB[s_pb[b] + i] |= ROW_SHARED;
+            }
+        }
+        __syncwarp();
     }
+}
+
+// the scanned totals of every block (entries, then runs) for the host
+__global__ void k_block_totals(const int32_t* cnt, int nb, int64_t T1, int32_t* out) {
+    const int i = threadIdx.x;
+    if (i < 2 * nb) out[i] = cnt[(int64_t)i * T1 + (T1 - 1)];
 }
 
 // exclusive scan of nb segments of L = n+1 int32 each (block-major), in
@@ -890,29 +716,31 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_apply(const int32_t* in, 
     }
 }
 
-// segments 1..nb: the column blocks of graph 0, which keeps only its
-// grandparent tiles; block b's rows are rpB[b] over colB + (entries before b)
-__global__ void k_setup_blocks(Ctx* ctx, const int32_t* rpB, const int32_t* colB, int nb, int32_t k2_tile) {
+// segments 1..nb: the column blocks of graph 0 (compressed rows: block b's
+// runs are its rows, rowsB maps them to the graph's rows), which keeps only
+// its grandparent tiles
+__global__ void k_setup_blocks(Ctx* ctx, BlockLayout L, const int32_t* colB, const int32_t* rowsB,
+                               const int32_t* endsB, int32_t k2_tile) {
     Seg* segs = ctx->segs;
     const Seg g = segs[0];
-    const int64_t np1 = g.n + 1;
-    int64_t base = 0;
-    for (int b = 0; b < nb; ++b) {
-        const int64_t mb = rpB[(int64_t)b * np1 + g.n];
+    for (int b = 0; b < L.nb; ++b) {
+        const int64_t pb = L.pbase[b + 1] - L.pbase[b];
+        const int64_t mb = L.ebase[b + 1] - L.ebase[b];
         Seg s = g;
-        s.rp = rpB + (int64_t)b * np1;
-        s.ci = colB + base;
+        s.rp = endsB + L.pbase[b] + b;
+        s.ci = colB + L.ebase[b];
+        s.rowmap = rowsB + L.pbase[b];
+        s.n = pb;
         s.m = mb;
-        s.k2_ntiles = mb > 0 ? (int32_t)((g.n + mb + k2_tile - 1) / k2_tile) : 0;
+        s.k2_ntiles = mb > 0 ? (int32_t)((pb + mb + k2_tile - 1) / k2_tile) : 0;
         s.k3_ntiles = 0;
         s.active = 1;
         s.leader = 0;
         s.user = b;
         segs[1 + b] = s;
-        base += mb;
     }
     segs[0].k2_ntiles = 0;
-    ctx->num_segs = nb + 1;
+    ctx->num_segs = L.nb + 1;
     ctx->k2_tile = k2_tile;
     ctx->loop_iter = 0;  // an iteration run before the blocks is not the device loop's
 }
@@ -920,11 +748,6 @@ __global__ void k_setup_blocks(Ctx* ctx, const int32_t* rpB, const int32_t* colB
 // ---------------------------------------------------------------------------
 // K2: SpMV (select2nd, min) fused with the three hooks
 // ---------------------------------------------------------------------------
-
-template <int THREADS, int ITEMS>
-constexpr int k2_smem_bytes() {
-    return (2 * (THREADS * ITEMS + 1) + THREADS * ITEMS) * (int)sizeof(int32_t);
-}
 
 // first kernel of every iteration: resets the loop condition to "stop" (only
 // the last CTA of k3_grandparent sets it back to "continue" when work
@@ -950,11 +773,14 @@ __global__ void k_iter_begin(Ctx* __restrict__ ctx, cudaGraphConditionalHandle c
 // tile, merged by atomic min into mngf.
 //
 // block < 0: every tile of every segment (no column blocking).  block >= 0:
-// only the tiles of column block `block` of graph 0; the blocks of a graph
-// run as consecutive launches, so a row's minimum from this block can be
-// merged into mngf with a plain load-min-store.
+// only the tiles of column block `block` of graph 0, whose rows are the
+// block's runs (rowmap gives each run's graph row); every run's minimum
+// merges by a fire-and-forget atomic min (no load round trip in the tile).
+// A launch over one segment (a column block, or a single graph) reads the
+// segment's fields once, and every tile reads the next tile's merge-path
+// start rows ahead, so a tile's only waits are its column ids and gathers.
 template <typename RP, int THREADS, int ITEMS>
-__global__ void __launch_bounds__(THREADS) k2_spmv(Ctx* __restrict__ ctx, int block) {
+__global__ void __launch_bounds__(THREADS, 1536 / THREADS) k2_spmv(Ctx* __restrict__ ctx, int block) {
     constexpr int TILE = THREADS * ITEMS;
     if (!(ctx->mode & MODE_DENSE)) return;
     extern __shared__ int32_t smem[];
@@ -965,17 +791,47 @@ __global__ void __launch_bounds__(THREADS) k2_spmv(Ctx* __restrict__ ctx, int bl
     const int32_t* __restrict__ tile_seg = ctx->k2_tile_seg;
     const int32_t* __restrict__ tile_row = ctx->k2_tile_row;
     const Seg* __restrict__ segs = ctx->segs;
-    int64_t t_begin = 0, T = ctx->k2_total;
+    const int64_t total = ctx->k2_total;
+    int64_t t_begin = 0, T = total;
     if (block >= 0) {
         if (block + 1 >= ctx->num_segs) return;
         t_begin = segs[1 + block].k2_tile0;
         T = t_begin + segs[1 + block].k2_ntiles;
     }
     const bool merge = block >= 0;
+    // one segment for the whole launch (a column block, or a single graph):
+    // its state is checked once and no tile looks its segment up
+    const bool one_seg = block >= 0 || ctx->num_segs == 1;
+    const int32_t seg0 = block >= 0 ? 1 + block : 0;
+    bool ident1 = false;
+    int64_t ncol1 = 0;
+    if (one_seg) {
+        const Seg& L = segs[segs[seg0].leader];
+        if (!L.active || L.mode != 0) return;
+        ident1 = L.iters == 0;
+        ncol1 = L.n;
+    }
+    int64_t t = t_begin + blockIdx.x;
+    int32_t xa = t < T ? tile_row[t] : 0, xb = t + 1 < total ? tile_row[t + 1] : 0;
 
-    for (int64_t t = t_begin + blockIdx.x; t < T; t += gridDim.x) {
-        const Seg* S = segs + tile_seg[t];
-        if (!segs[S->leader].active || segs[S->leader].mode != 0) continue;
+    for (; t < T; t += gridDim.x) {
+        // this tile's merge-path start rows, and the next tile's, read ahead
+        const int32_t xr0 = xa, xr1 = xb;
+        const int64_t tn = t + gridDim.x;
+        if (tn < T) {
+            xa = tile_row[tn];
+            xb = tn + 1 < total ? tile_row[tn + 1] : 0;
+        }
+        const Seg* S = segs + seg0;
+        bool ident = ident1;
+        int64_t ncol = ncol1;
+        if (!one_seg) {
+            S = segs + tile_seg[t];
+            const Seg& L = segs[S->leader];
+            if (!L.active || L.mode != 0) continue;
+            ident = L.iters == 0;
+            ncol = L.n;
+        }
         const RP* __restrict__ rp = (const RP*)S->rp;
         const int32_t* __restrict__ gf = S->gf;
         int32_t* mngf = S->mngf;
@@ -983,8 +839,8 @@ __global__ void __launch_bounds__(THREADS) k2_spmv(Ctx* __restrict__ ctx, int bl
         const int64_t lt = t - S->k2_tile0;
         const int64_t d0 = lt * TILE;
         const int64_t d1 = min(d0 + (int64_t)TILE, n + m);
-        const int64_t x0 = tile_row[t];
-        const int64_t x1 = (lt + 1 < S->k2_ntiles) ? (int64_t)tile_row[t + 1] : n;
+        const int64_t x0 = xr0;
+        const int64_t x1 = (lt + 1 < S->k2_ntiles) ? (int64_t)xr1 : n;
         if (x1 < x0) continue;  // only possible for a malformed row_ptr
         const int64_t y0 = d0 - x0, y1 = d1 - x1;
         const int nfull = (int)(x1 - x0);            // rows whose end lies in this tile
@@ -993,11 +849,10 @@ __global__ void __launch_bounds__(THREADS) k2_spmv(Ctx* __restrict__ ctx, int bl
         const int D = (int)(d1 - d0);
         const RP* __restrict__ rpt = rp + x0 + 1;     // row ends of the tile's rows
         const int32_t* __restrict__ cit = S->ci + y0; // the tile's entries
-        // first iteration of the graph: gf is still the identity (every
-        // vertex its own root), so gf[v] = v and the gather is skipped
-        const bool ident = segs[S->leader].iters == 0;
 
-        // phase 1: row ends, and the gathered grandparents of the tile's entries
+        // phase 1: row ends, and the gathered grandparents of the tile's
+        // entries (in the graph's first iteration gf is still the identity:
+        // every vertex its own root, so gf[v] = v and nothing is gathered)
         for (int i = tid; i < R; i += THREADS) {
             int64_t e = rp_at(rpt, i);
             e = (e < y1 ? e : y1) - y0;
@@ -1014,7 +869,7 @@ __global__ void __launch_bounds__(THREADS) k2_spmv(Ctx* __restrict__ ctx, int bl
 #pragma unroll
             for (int q = 0; q < ITEMS; ++q) {
                 const int j = tid + q * THREADS;
-                if (j < E) s_val[j] = ((uint32_t)c[q] < (uint64_t)n) ? (ident ? c[q] : __ldg(gf + c[q])) : INF;
+                if (j < E) s_val[j] = ((uint32_t)c[q] < (uint64_t)ncol) ? (ident ? c[q] : __ldg(gf + c[q])) : INF;
             }
         }
         __syncthreads();
@@ -1067,61 +922,83 @@ __global__ void __launch_bounds__(THREADS) k2_spmv(Ctx* __restrict__ ctx, int bl
         __syncthreads();
 
         // phase 3: the tile's row minima into mngf.  A row that starts and
-        // ends inside this tile has its complete minimum here: a plain store
-        // (or, for a column block, a plain load-min-store, since no other
-        // launch runs at the same time).  Only the first and last row of a
-        // tile can continue in a neighbouring tile; those merge by atomic min.
-        // (Atomic merges of every row measured 2.6x slower on this kernel.)
-        const bool first_whole = rp_at(rp, x0) >= y0;
-        for (int i = tid; i < R; i += THREADS) {
-            const int32_t mn = s_mngf[i];
-            const bool whole = i < nfull && (i > 0 || first_whole);
-            if (whole) {
-                if (!merge)
+        // ends inside this tile has its complete minimum here: a plain store.
+        // Only the first and last row of a tile can continue in a
+        // neighbouring tile; those merge by atomic min.  (Atomic merges of
+        // every row measured 2.6x slower on this kernel.)  A column block's
+        // runs all merge by atomic min without a return value.
+        if (!merge) {
+            const bool first_whole = rp_at(rp, x0) >= y0;
+            for (int i = tid; i < R; i += THREADS) {
+                const int32_t mn = s_mngf[i];
+                if (i < nfull && (i > 0 || first_whole))
                     mngf[x0 + i] = mn;
-                else if (mn != INF && mn < mngf[x0 + i])  // a row without entries in this block reads nothing
-                    mngf[x0 + i] = mn;
-            } else if (mn != INF) {
-                atomicMin(mngf + x0 + i, mn);
+                else if (mn != INF)
+                    atomicMin(mngf + x0 + i, mn);
+            }
+        } else {
+            const int32_t* __restrict__ rowmap = S->rowmap + x0;
+            for (int i = tid; i < R; i += THREADS) {
+                const int32_t mn = s_mngf[i];
+                if (mn == INF) continue;
+                const int32_t u = rowmap[i] & 0x7fffffff;
+                if (u < ncol) atomicMin(mngf + u, mn);
             }
         }
         __syncthreads();
     }
 }
 
+template <int THREADS, int ITEMS>
+constexpr int k2_smem_bytes() {
+    return (2 * (THREADS * ITEMS + 1) + THREADS * ITEMS) * (int)sizeof(int32_t);
+}
+
 // a1 in the first iteration of a column-blocked solve, on the graph's own
 // CSR (segment 0, its merge-path tiles of FIRST_THREADS x FIRST_ITEMS
 // items): gf is still the identity (Algorithm 2 starts from f[u] = u), so
 // mngf[u] is u's smallest neighbour id and nothing is gathered.  The same
-// pass counts into *descents the adjacent entry pairs of a row that are in
-// decreasing order as unsigned ids: every adjacent pair ending in the tile
-// (striped over the threads, off the walk's serial loop), minus the pairs
-// that end at a row's first entry.  Zero exactly when every row is sorted,
-// the test that picks how the block copy is built.
+// pass counts, per tile and column block, the tile's entries and runs (see
+// the block copy's layout) into cnt[b][t] and cnt[nb + b][t] (rows of
+// tiles + 1 entries; the last entry of each row is 0, so that an exclusive
+// scan of the row ends in the row's total).  The counts are taken striped
+// over the tile's entries with warp ballots, off the walk's serial loop.
 constexpr int FIRST_THREADS = 64;
 constexpr int FIRST_ITEMS = 16;
+static_assert(FIRST_THREADS * FIRST_ITEMS == BUILD_TILE, "the block copy cuts along the first iteration's tiles");
+static_assert(FIRST_THREADS >= 2 * MAX_COL_BLOCKS, "one thread per count of a tile");
 
 template <typename RP>
 __global__ void __launch_bounds__(FIRST_THREADS)
-    k2_first(Ctx* __restrict__ ctx, unsigned long long* __restrict__ descents) {
+    k2_first(Ctx* __restrict__ ctx, int32_t* __restrict__ cnt, int nb, int shift) {
     constexpr int THREADS = FIRST_THREADS, ITEMS = FIRST_ITEMS, TILE = THREADS * ITEMS;
     extern __shared__ int32_t smem[];
     int32_t* s_rowend = smem;                // local end offset of each row in the tile
     int32_t* s_mngf = smem + (TILE + 1);     // per-row minimum over the tile's entries
     int32_t* s_col = smem + 2 * (TILE + 1);  // the tile's column ids as given
-    const int tid = threadIdx.x;
+    __shared__ unsigned s_rs[TILE / 32];     // bit j: entry j is the first entry of a row
+    __shared__ int s_cnt[2 * MAX_COL_BLOCKS];
+    const int tid = threadIdx.x, lane = tid & 31;
     const Seg* __restrict__ S = ctx->segs;
     const RP* __restrict__ rp = (const RP*)S->rp;
     int32_t* mngf = S->mngf;
     const int64_t n = S->n, m = S->m;
-    int desc = 0;
+    const bool count = cnt != nullptr;
+    const int64_t T1 = (int64_t)S->k2_ntiles + 1;
+    if (count && blockIdx.x == 0 && tid < 2 * nb) cnt[(int64_t)tid * T1 + T1 - 1] = 0;
+    if (tid < TILE / 32) s_rs[tid] = 0u;
+    if (tid < 2 * MAX_COL_BLOCKS) s_cnt[tid] = 0;
+    __syncthreads();
     for (int64_t lt = blockIdx.x; lt < S->k2_ntiles; lt += gridDim.x) {
         const int64_t t = S->k2_tile0 + lt;
         const int64_t d0 = lt * TILE;
         const int64_t d1 = min(d0 + (int64_t)TILE, n + m);
         const int64_t x0 = ctx->k2_tile_row[t];
         const int64_t x1 = (lt + 1 < S->k2_ntiles) ? (int64_t)ctx->k2_tile_row[t + 1] : n;
-        if (x1 < x0) continue;  // only possible for a malformed row_ptr
+        if (x1 < x0) {  // only possible for a malformed row_ptr
+            if (count && tid < 2 * nb) cnt[(int64_t)tid * T1 + lt] = 0;
+            continue;
+        }
         const int64_t y0 = d0 - x0, y1 = d1 - x1;
         const int nfull = (int)(x1 - x0);
         const int R = nfull + (x1 < n ? 1 : 0);
@@ -1133,8 +1010,10 @@ __global__ void __launch_bounds__(FIRST_THREADS)
         for (int i = tid; i < R; i += THREADS) {
             int64_t e = rp_at(rpt, i);
             e = (e < y1 ? e : y1) - y0;
-            s_rowend[i] = (int32_t)(e < 0 ? 0 : e);
+            const int ev = (int)(e < 0 ? 0 : e);
+            s_rowend[i] = ev;
             s_mngf[i] = INF;
+            if (count && i < nfull && ev < E) atomicOr(&s_rs[ev >> 5], 1u << (ev & 31));  // row i + 1 starts at ev
         }
         {
             int32_t c[ITEMS];
@@ -1151,8 +1030,7 @@ __global__ void __launch_bounds__(FIRST_THREADS)
         }
         __syncthreads();
 
-        // the merge-path walk of k2_spmv over ITEMS items per thread; rstart
-        // is the tile-local first entry of the open row
+        // the merge-path walk of k2_spmv over ITEMS items per thread
         const int k0 = tid * ITEMS;
         int r = -1;
         int32_t acc = INF;
@@ -1192,24 +1070,30 @@ __global__ void __launch_bounds__(FIRST_THREADS)
                 atomicMin(&s_mngf[key], acc);
             }
         }
-        // descending pairs: every adjacent pair ending in this tile, minus
-        // those that cross into a row's first entry
-        const bool first_whole = rp_at(rp, x0) >= y0;
-        const uint32_t before = (y0 > 0 && E > 0) ? (uint32_t)__ldg(S->ci + y0 - 1) : 0u;
-        for (int j = tid; j < E; j += THREADS)
-            desc += (int)((j > 0 ? (uint32_t)s_col[j - 1] : before) > (uint32_t)s_col[j]);
-        for (int i = tid; i < R; i += THREADS) {
-            if (i == 0 && !first_whole) continue;  // row x0 began in an earlier tile
-            const int st = i == 0 ? 0 : s_rowend[i - 1];
-            const int en = i < nfull ? s_rowend[i] : E;
-            if (st < en && y0 + st > 0)
-                desc -= (int)((st > 0 ? (uint32_t)s_col[st - 1] : before) > (uint32_t)s_col[st]);
+        if (count) {
+            // entries and run starts per column block, in rounds of 32
+            // entries striped over the warps: the lanes of one block find
+            // each other with a match, and the group's first lane counts them
+            for (int base = (tid >> 5) * 32; base < E; base += THREADS) {
+                const int j = base + lane;
+                const bool valid = j < E;
+                const int b = valid ? col_block(s_col[j], shift, nb) : 0;
+                const bool rs = valid && run_start(s_col, s_rs, j, b, shift, nb);
+                const unsigned grp = __match_any_sync(0xffffffffu, valid ? b : 64 + lane);
+                const unsigned rsb = __ballot_sync(0xffffffffu, rs);
+                if (valid && (__ffs(grp) - 1) == lane) {
+                    atomicAdd(&s_cnt[b], __popc(grp));
+                    const int rn = __popc(grp & rsb);
+                    if (rn) atomicAdd(&s_cnt[MAX_COL_BLOCKS + b], rn);
+                }
+            }
         }
         __syncthreads();
 
         // row minima into mngf: rows whole in the tile by plain stores, the
         // first and last row (they may continue in a neighbouring tile) by
         // atomic min
+        const bool first_whole = rp_at(rp, x0) >= y0;
         for (int i = tid; i < R; i += THREADS) {
             const int32_t mn = s_mngf[i];
             if (i < nfull && (i > 0 || first_whole))
@@ -1217,11 +1101,16 @@ __global__ void __launch_bounds__(FIRST_THREADS)
             else if (mn != INF)
                 atomicMin(mngf + x0 + i, mn);
         }
+        if (count) {
+            if (tid < nb) cnt[(int64_t)tid * T1 + lt] = s_cnt[tid];
+            else if (tid >= MAX_COL_BLOCKS && tid < MAX_COL_BLOCKS + nb)
+                cnt[(int64_t)(nb + tid - MAX_COL_BLOCKS) * T1 + lt] = s_cnt[tid];
+        }
+        __syncthreads();
+        if (tid < TILE / 32) s_rs[tid] = 0u;
+        if (tid < 2 * MAX_COL_BLOCKS) s_cnt[tid] = 0;
         __syncthreads();
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) desc += __shfl_down_sync(0xffffffffu, desc, o);
-    if ((tid & 31) == 0 && desc) atomicAdd(descents, (unsigned long long)(long long)desc);
 }
 
 __host__ __device__ constexpr int k2_first_smem() { return (3 * (FIRST_THREADS * FIRST_ITEMS) + 2) * (int)sizeof(int32_t); }

@@ -39,6 +39,8 @@ struct Seg {
     int32_t mode;        // this iteration: 0 = full SpMV, 1 = push from the frontier
     int32_t* mngf;       // per-row minimum of gf over neighbours, kept across iterations
     unsigned long long fr_deg;  // degree sum of this iteration's changed vertices (being filled)
+    const int32_t* rowmap;  // column block of a graph: the graph row of each local row (a run of
+                            // entries; bit 31 set: merge its minimum atomically); nullptr: identity
 };
 
 // Ctx::mode bits: some active graph runs a full SpMV / pushes this iteration

@@ -71,6 +71,7 @@ __global__ void k_pool_admit(Ctx* ctx, Seg* segs, int32_t* k2_seg, int32_t* k2_r
         s.mode = 0;  // a restored graph's mngf is not kept: its first step runs a full SpMV
         s.mngf = a.mngf;
         s.fr_deg = 0;
+        s.rowmap = nullptr;
         segs[a.slot] = s;
     }
     if (i == 0) {
@@ -122,6 +123,7 @@ __global__ void k_pool_begin(Ctx* ctx, int32_t loop_limit, int32_t* frontier, in
 
 struct Slot {
     int state = 0;  // 0 free, 1 admitted (copies in flight), 2 iterating on the device
+    cudaEvent_t copied = nullptr;  // recorded on the copy stream after the slot's copies
     int64_t n = 0, m = 0;
     size_t off = 0, bytes = 0;
     int32_t* labels_host = nullptr;
@@ -159,7 +161,7 @@ struct Pool {
     std::vector<int> admitted;  // slots whose copies were enqueued since the last step
     cudaStream_t copy_stream = nullptr;  // admissions (host to device), may run during a step
     cudaStream_t out_stream = nullptr;   // harvests (labels to host)
-    cudaEvent_t copy_done = nullptr, step_done = nullptr;
+    cudaEvent_t step_done = nullptr;
     cudaEvent_t ev_t[4] = {};  // step phases: start, copies landed, set-up done, loop done
     bool timed = false;        // the last step recorded ev_t
     bool stepped = false;
@@ -167,6 +169,13 @@ struct Pool {
 };
 
 static size_t align_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
+
+// a slot back to free (its copy event is kept for the next graph)
+static void slot_reset(Slot& S) {
+    cudaEvent_t ev = S.copied;
+    S = Slot();
+    S.copied = ev;
+}
 
 static size_t region_bytes(int64_t n, int64_t m) {
     return align_up((size_t)(n + 1) * 4) + align_up((size_t)(m > 0 ? m : 1) * 4) + 4 * align_up((size_t)n * 4);
@@ -225,10 +234,11 @@ void pool_release(fastsv_ctx* h) {
     if (P->arena) cudaFree(P->arena);
     if (P->copy_stream) cudaStreamDestroy(P->copy_stream);
     if (P->out_stream) cudaStreamDestroy(P->out_stream);
-    if (P->copy_done) cudaEventDestroy(P->copy_done);
     if (P->step_done) cudaEventDestroy(P->step_done);
     for (cudaEvent_t& ev : P->ev_t)
         if (ev) cudaEventDestroy(ev);
+    for (Slot& S : P->slots)
+        if (S.copied) cudaEventDestroy(S.copied);
     delete P;
     h->pool = nullptr;
 }
@@ -286,9 +296,10 @@ fastsv_status fastsv_pool_create(fastsv_t h, size_t budget, int32_t max_slots) {
     if (e == cudaSuccess) e = cudaMallocHost((void**)&P->h_segs, sizeof(Seg) * (size_t)max_slots);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->copy_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->out_stream, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->copy_done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->step_done, cudaEventDisableTiming);
     for (int i = 0; i < 4 && e == cudaSuccess && h->opt.timing; ++i) e = cudaEventCreate(&P->ev_t[i]);
+    for (int i = 0; i < max_slots && e == cudaSuccess; ++i)
+        e = cudaEventCreateWithFlags(&P->slots[i].copied, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         st = cuda_fail(h, e);
         pool_release(h);
@@ -354,9 +365,10 @@ static fastsv_status admit(fastsv_t h, int64_t n, const int32_t* rp, const int32
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(base + off_gf(n, m), gh, (size_t)n * 4, cudaMemcpyHostToDevice, P->copy_stream);
     }
+    if (e == cudaSuccess) e = cudaEventRecord(S.copied, P->copy_stream);
     if (e != cudaSuccess) {
         arena_free(P, off, bytes);
-        S = Slot();
+        slot_reset(S);
         return cuda_fail(h, e);
     }
     P->admitted.push_back(slot);
@@ -423,7 +435,7 @@ fastsv_status fastsv_pool_evict(fastsv_t h, int32_t slot, void* checkpoint_host)
     P->h_segs[slot].active = 0;
     P->dirty = true;  // its tiles leave the lists at the next step
     arena_free(P, S.off, S.bytes);
-    S = Slot();
+    slot_reset(S);
     return FASTSV_OK;
 }
 
@@ -437,17 +449,42 @@ fastsv_status fastsv_pool_step(fastsv_t h, int32_t iters, void* stream) {
     if (!h || !h->pool || iters < 1) return FASTSV_ERR_INVALID_ARG;
     Pool* P = h->pool;
     cudaStream_t s = (cudaStream_t)stream;
+    h->opt = h->base_opt;  // pools run the handle's own options (no tuning-cache lookup)
+    h->last_tuned = 0;
     const int items = k2_items(h);
     const int32_t tile = (int32_t)k2_tile(h);
     // the slot snapshot read below must be the previous step's final one
     if (P->stepped) FSV_CUDA(h, cudaEventSynchronize(P->step_done));
     const bool timed = P->ev_t[0] != nullptr;
     if (timed) FSV_CUDA(h, cudaEventRecord(P->ev_t[0], s));
-    size_t na = P->admitted.size();
-    if (na > 0) {
-        FSV_CUDA(h, cudaEventRecord(P->copy_done, P->copy_stream));
-        FSV_CUDA(h, cudaStreamWaitEvent(s, P->copy_done, 0));
+    // graphs whose copies have landed join this step; the others keep
+    // copying while it runs and join a later one.  If nothing would run,
+    // the step waits for the first admitted graph's copies instead.
+    std::vector<int> joining, later;
+    for (int slot : P->admitted) {
+        if (h->opt.pool_wait_copies) {
+            FSV_CUDA(h, cudaStreamWaitEvent(s, P->slots[slot].copied, 0));
+            joining.push_back(slot);
+            continue;
+        }
+        const cudaError_t q = cudaEventQuery(P->slots[slot].copied);
+        if (q == cudaSuccess)
+            joining.push_back(slot);
+        else if (q == cudaErrorNotReady)
+            later.push_back(slot);
+        else
+            return cuda_fail(h, q);
     }
+    bool resident = false;
+    for (int i = 0; i < P->max_slots && !resident; ++i)
+        resident = P->slots[i].state == 2 && P->h_segs[i].active;
+    if (joining.empty() && !resident && !later.empty()) {
+        joining.push_back(later.front());
+        later.erase(later.begin());
+        FSV_CUDA(h, cudaStreamWaitEvent(s, P->slots[joining[0]].copied, 0));
+    }
+    P->admitted = joining;
+    size_t na = P->admitted.size();
     if (timed) FSV_CUDA(h, cudaEventRecord(P->ev_t[1], s));
     size_t done = 0;
     do {
@@ -484,7 +521,7 @@ fastsv_status fastsv_pool_step(fastsv_t h, int32_t iters, void* stream) {
         FSV_CUDA(h, cudaGetLastError());
     } while (done < na);
     if (na > 0) P->dirty = true;
-    P->admitted.clear();
+    P->admitted = later;
     if (P->dirty) {
         fastsv_status st = rebuild_tiles(h, P->d_ctx, s);
         if (st != FASTSV_OK) return st;
@@ -492,9 +529,7 @@ fastsv_status fastsv_pool_step(fastsv_t h, int32_t iters, void* stream) {
     }
     // work remains if graphs were just admitted or the last step's snapshot
     // shows a resident slot still iterating
-    bool any = na > 0;
-    for (int i = 0; i < P->max_slots && !any; ++i)
-        any = P->slots[i].state == 2 && P->h_segs[i].active;
+    bool any = na > 0 || resident;
     if (timed) FSV_CUDA(h, cudaEventRecord(P->ev_t[2], s));
     if (any) {
         h->loop_limit_host = iters;
@@ -565,7 +600,7 @@ fastsv_status fastsv_pool_poll(fastsv_t h, int32_t* done_slots, int32_t* done_it
         for (int i : harvested) {
             Slot& S = P->slots[i];
             arena_free(P, S.off, S.bytes);
-            S = Slot();
+            slot_reset(S);
         }
         P->dirty = true;  // the next step's tile lists leave the finished graphs out
     }

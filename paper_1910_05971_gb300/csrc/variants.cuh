@@ -124,6 +124,12 @@ __device__ __forceinline__ int32_t ld_live(const int32_t* p) { return *p; }
 // it is read and lowered by atomics in the same kernel.  The counter receives, per tile, the
 // number of rows whose processing lowered some entry of f (at most one per
 // row and tile, so it cannot wrap).
+// shared memory of k_async: row ends, row minima, gathered values of a tile
+template <int THREADS, int ITEMS>
+constexpr int async_smem_bytes() {
+    return (2 * (THREADS * ITEMS + 1) + THREADS * ITEMS) * (int)sizeof(int32_t);
+}
+
 template <typename RP, int THREADS, int ITEMS>
 __global__ void __launch_bounds__(THREADS, 5) k_async(Ctx* __restrict__ ctx) {
     constexpr int TILE = THREADS * ITEMS;

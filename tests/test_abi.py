@@ -38,8 +38,8 @@ def test_host_only_entry_points():
     import paper_1910_05971_gb300 as fsv
     o = fsv.fastsv_default_options()
     assert (o.rowptr_bits, o.mode, o.max_iters, o.use_graph, o.k2_items) == (64, 0, 4096, 1, 8)
-    assert C.sizeof(fsv.fastsv_options) == 64
-    assert C.sizeof(fsv.fastsv_stats) == 592
+    assert C.sizeof(fsv.fastsv_options) == 72
+    assert C.sizeof(fsv.fastsv_stats) == 608
     assert fsv.fastsv_status_string(fsv.FASTSV_ERR_MAX_ITERS) == "FASTSV_ERR_MAX_ITERS"
     assert fsv.fastsv_pool_bytes(10, 20) > 0
     # invalid handles are rejected on the host without touching a device

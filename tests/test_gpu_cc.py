@@ -94,10 +94,10 @@ def test_column_blocks_with_unsorted_rows():
 @pytest.mark.parametrize("k", [2, 3])
 def test_column_blocks_with_one_descent_at_a_tile_boundary(k):
     """The only unsorted pair of the graph lies in a hub row and straddles a
-    boundary of the 1024-item merge-path tiles the first iteration walks
-    (where the sortedness count reads the previous tile's last entry), with
-    its two ids in different column blocks: the block copy must notice it
-    and still reproduce Algorithm 2."""
+    boundary of the 1024-item merge-path tiles along which the block copy is
+    cut, with its two ids in different column blocks: the hub's runs of one
+    block then come from several tiles and must merge atomically, and the
+    solve must still reproduce Algorithm 2."""
     n = 4096
     row0 = [1] + list(range(3001, 4024))      # 1024 entries: the hub's row starts at entry 1024
     hub = [0] + list(range(2, 3001))          # vertex 1
@@ -258,9 +258,10 @@ def test_launch_count_over_unsynchronised_calls(col_blocks):
             assert one == 4 + 5 * it
         else:
             # set-up (3), the first iteration on the original CSR (4), the
-            # block build (10) and the blocks' set-up (3), finish (1); then
-            # 4 + col_blocks kernels per device-loop iteration
-            assert one == 21 + (4 + col_blocks) * (it - 1)
+            # scan of its block counts and their totals (4), the block split
+            # and the blocks' set-up (4), finish (1); then 4 + col_blocks
+            # kernels per device-loop iteration
+            assert one == 16 + (4 + col_blocks) * (it - 1)
         for _ in range(5):
             s.cc(rp_d, ci_d, lab, check_status=False)
         s.check_last()
@@ -332,3 +333,30 @@ def test_sparse_iterations_are_used_and_exact():
     assert st_a["sparse_iters"] == itg - 1
     for got, st, ref, n_it, trace in ((dense, st_d, f, it, ch), (sparse, st_s, f, it, ch), (always, st_a, fg, itg, chg)):
         assert np.array_equal(got, ref) and st["iterations"] == n_it and st["changed_per_iter"] == trace.tolist()
+
+
+def test_tuning_cache_entry_is_applied(tmp_path):
+    """A tuning-cache entry for the call's shape class replaces the kernel
+    choices (here: column blocks and tile shape forced, pushes off); the
+    result stays Algorithm 2's, iteration by iteration."""
+    import paper_1910_05971_gb300 as fsv
+    from paper_1910_05971_gb300 import tune
+    rp, ci = graphgen.rmat(12, 16, seed=6, permute=True)
+    f, it, _, ch = oracle.fastsv(rp, ci)
+    key = fsv.fastsv_tune_key(fsv.TUNE_SINGLE, len(rp) - 1, len(ci), 1, 64)
+    path = str(tmp_path / "cache.txt")
+    tune.write_cache(path, {key: dict(k2_items=16, k2_threads=64, col_blocks=4, sparse_div=0, batch_sparse_div=0)})
+    with fsv.FastSV(tune_cache=path) as s:
+        lab = s.cc(to_dev(rp), to_dev(ci))
+        st = s.stats()
+    assert st["tuned"] and st["col_blocks"] == 4 and st["sparse_iters"] == 0 and st["block_runs"] > 0
+    assert np.array_equal(lab.cpu().numpy(), f) and st["iterations"] == it
+    assert st["changed_per_iter"] == ch.tolist()
+    rp2, ci2 = graphgen.rmat(10, 8, seed=1)  # another shape class: the handle's own options
+    with fsv.FastSV(tune_cache=path) as s:
+        lab2 = s.cc(to_dev(rp2), to_dev(ci2))
+        st2 = s.stats()
+    assert not st2["tuned"] and st2["col_blocks"] == 1
+    assert np.array_equal(lab2.cpu().numpy(), oracle.uf(rp2, ci2))
+    with pytest.raises(fsv.FastSVError):
+        fsv.FastSV(tune_cache=str(tmp_path / "missing.txt"))

@@ -154,8 +154,10 @@ def test_evict_and_restore_resume_exactly():
     graphs = [(rp.astype(np.int32), ci.astype(np.int32)) for rp, ci in graphs]
     ref = _alone(graphs)
     assert all(it > 3 for _, it in ref)  # all still iterating after two steps
-    pool = PoolBackend(64 << 20, 8)
-    other = PoolBackend(64 << 20, 8)
+    # every graph added before a step takes part in it (the checkpoints are
+    # compared after exactly two iterations)
+    pool = PoolBackend(64 << 20, 8, pool_wait_copies=True)
+    other = PoolBackend(64 << 20, 8, pool_wait_copies=True)
     labels = [np.full(len(rp) - 1, -1, np.int32) for rp, _ in graphs]
     slot_of = {}
     for g, (rp, ci) in enumerate(graphs):
@@ -204,7 +206,7 @@ def test_evict_and_restore_errors():
     rp, ci = rp.astype(np.int32), ci.astype(np.int32)
     small = oracle.csr_from_edges(2, [(0, 1)])
     small = (small[0].astype(np.int32), small[1].astype(np.int32))
-    pool = PoolBackend(16 << 20, 4)
+    pool = PoolBackend(16 << 20, 4, pool_wait_copies=True)  # graphs added before a step take part in it
     lab = np.empty(len(rp) - 1, np.int32)
     buf = np.zeros(fsv.fastsv_pool_checkpoint_bytes(len(rp) - 1), np.uint8)
     assert fsv.fastsv_pool_evict(pool.h, 0, buf.ctypes.data) == fsv.FASTSV_ERR_INVALID_ARG  # free slot
