@@ -129,10 +129,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fastsv", choices=["fastsv", "reference"])
     ap.add_argument("--workload", default="rmat_s26_perm", choices=sorted(WORKLOADS))
-    ap.add_argument("--k2-items", type=int, default=8)
+    ap.add_argument("--k2-items", type=int, default=None,
+                    help="SpMV items per thread (default: the library's choice, or the tuning cache's)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--col-blocks", type=int, default=0)
+    ap.add_argument("--col-blocks", type=int, default=None,
+                    help="column blocks (default: the library's choice, or the tuning cache's)")
     ap.add_argument("--mode", default="single", choices=["single", "batched", "serve", "variants"],
                     help="single: one large graph (default, the headline); batched: 4096 ER graphs in one "
                          "launch vs per-graph launches; serve: replay of the request trace; variants: "
@@ -145,7 +147,7 @@ def main():
                     help="serve: distinct request graphs materialised (arrival i carries graph i mod this)")
     ap.add_argument("--no-batched", action="store_true", help="single mode: leave out the batched measurement")
     ap.add_argument("--no-serve", action="store_true", help="single mode: leave out the serving measurement")
-    ap.add_argument("--batch-sparse-div", type=int, default=0,
+    ap.add_argument("--batch-sparse-div", type=int, default=None,
                     help="batched/serve modes: per-graph sparse iterations threshold (0 = off)")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -193,6 +195,7 @@ def main():
         solver.cc(rp_dev, ci_dev, labels)
     st = solver.stats()
     iterations = st["iterations"]
+    tune_key = fsv.fastsv_tune_key(fsv.TUNE_SINGLE, n, m, 1, bits)
 
     # ---- timed region: K solves, inputs resident in HBM (9 GB >> 129 MB L2) ----
     def barrier():
@@ -222,6 +225,23 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     value = world * m / (ms * 1e-3) / 1e9
+
+    # ---- the same steps with the library's hand-picked defaults (no tuning cache) ----
+    hand = fsv.FastSV(rowptr_bits=bits, tune_cache=None)
+    for _ in range(args.warmup):
+        hand.cc(rp_dev, ci_dev, labels)
+    torch.cuda.synchronize()
+    eh0, eh1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    eh0.record(stream)
+    for _ in range(args.steps):
+        hand.cc(rp_dev, ci_dev, labels, check_status=False)
+    eh1.record(stream)
+    torch.cuda.synchronize()
+    hand.check_last()
+    ms_hand = eh0.elapsed_time(eh1) / args.steps
+    hand.close()
+    tuning = {"key": tune_key, "tuned": bool(st["tuned"]), "ms_per_step": ms, "ms_per_step_hand_picked": ms_hand,
+              "cache": "paper_1910_05971_gb300/tune_cache.txt (written by paper_1910_05971_gb300/tune.py on GB300)"}
 
     # ---- dominant kernel: k2_spmv durations from CUDA events (host-loop pass) ----
     prof = fsv.FastSV(rowptr_bits=bits, k2_items=args.k2_items, col_blocks=args.col_blocks, use_graph=False)
@@ -262,7 +282,10 @@ def main():
         ci_h = torch.from_numpy(ci).pin_memory()
         lab_h = torch.empty(n, dtype=torch.int32).pin_memory()
         hsolver = fsv.FastSV(rowptr_bits=bits, k2_items=args.k2_items, col_blocks=args.col_blocks)
-        hsolver.cc_host(rp_h, ci_h, lab_h)
+        # warm-up: the first device transfers out of freshly pinned pages run
+        # at a fraction of the link's speed (first-touch mapping)
+        for _ in range(args.warmup):
+            hsolver.cc_host(rp_h, ci_h, lab_h)
         barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -354,6 +377,7 @@ def main():
             "e2e": e2e,
             "gpu_launches": int(launches),
             "clocks": clocks,
+            "tuning": tuning,
             "batched": batched,
             "serve": serve,
         }

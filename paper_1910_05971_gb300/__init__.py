@@ -60,16 +60,20 @@ def stats_dict(s: fastsv_stats) -> dict:
 class FastSV:
     """One library handle (one workspace).  Not thread-safe.
 
-    ``tune_cache``: path of a tuning cache ("default": the packaged cache, if
-    present; None: none), whose entries replace k2_items, k2_threads,
-    col_blocks, sparse_div and batch_sparse_div for the shape classes they
-    cover."""
+    The kernel choices k2_items, k2_threads, col_blocks, sparse_div and
+    batch_sparse_div default to None: the library's defaults, or, for a
+    graph whose shape class has an entry in the tuning cache, the tuned
+    values.  ``tune_cache``: path of a tuning cache ("default": the packaged
+    cache, if present; None: none).  Passing any of the five kernel choices
+    explicitly turns the default cache off, so that the values given are the
+    values used."""
 
     def __init__(self, rowptr_bits: int = 64, mode: int = FASTSV_MODE_SYNC, max_iters: int = 4096,
-                 validate: int = 0, use_graph: bool = True, k2_items: int = 8, grid_ctas_per_sm: int = 0,
-                 timing: bool = True, fail_alloc_after: int = 0, col_blocks: int = 0,
-                 k2_threads: int = 256, sparse_div: int = 2, variant: int = 0, batch_sparse_div: int = 0,
-                 col_block_mib: int = 32, pool_wait_copies: bool = False, tune_cache: str | None = "default"):
+                 validate: int = 0, use_graph: bool = True, k2_items: int | None = None, grid_ctas_per_sm: int = 0,
+                 timing: bool = True, fail_alloc_after: int = 0, col_blocks: int | None = None,
+                 k2_threads: int | None = None, sparse_div: int | None = None, variant: int = 0,
+                 batch_sparse_div: int | None = None, col_block_mib: int = 32, pool_wait_copies: bool = False,
+                 tune_cache: str | None = "default"):
         _torch()
         o = fastsv_default_options()
         o.rowptr_bits = rowptr_bits
@@ -77,19 +81,20 @@ class FastSV:
         o.max_iters = max_iters
         o.validate = validate
         o.use_graph = int(use_graph)
-        o.k2_items = k2_items
         o.grid_ctas_per_sm = grid_ctas_per_sm
         o.timing = int(timing)
         o.fail_alloc_after = fail_alloc_after
-        o.col_blocks = col_blocks
-        o.k2_threads = k2_threads
-        o.sparse_div = sparse_div
         o.variant = variant
-        o.batch_sparse_div = batch_sparse_div
         o.col_block_mib = col_block_mib
         o.pool_wait_copies = int(pool_wait_copies)
+        chosen = dict(k2_items=k2_items, k2_threads=k2_threads, col_blocks=col_blocks, sparse_div=sparse_div,
+                      batch_sparse_div=batch_sparse_div)
+        for name, value in chosen.items():
+            if value is not None:
+                setattr(o, name, value)
         if tune_cache == "default":
-            tune_cache = DEFAULT_TUNE_CACHE if os.path.exists(DEFAULT_TUNE_CACHE) else None
+            explicit = any(v is not None for v in chosen.values())
+            tune_cache = DEFAULT_TUNE_CACHE if (os.path.exists(DEFAULT_TUNE_CACHE) and not explicit) else None
         self._tune_path = tune_cache.encode() if tune_cache else None  # kept alive for the call below
         o.tune_cache = self._tune_path
         self.options = o

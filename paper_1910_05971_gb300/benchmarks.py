@@ -29,7 +29,8 @@ def _clock_sampler(local_rank):
     return ClockSampler(local_rank)
 
 
-def batched_measure(graphs: int, steps: int, warmup: int, k2_items: int = 8, batch_sparse_div: int = 0,
+def batched_measure(graphs: int, steps: int, warmup: int, k2_items: int | None = None,
+                    batch_sparse_div: int | None = None,
                     local_rank: int = 0, dist=None, rank: int = 0, world: int = 1, sampler=None,
                     peak_gbs: float | None = None, peak_source: str = "") -> dict:
     """Config 4: one segmented solve of `graphs` Erdos-Renyi graphs (one device
@@ -92,7 +93,7 @@ def batched_measure(graphs: int, steps: int, warmup: int, k2_items: int = 8, bat
     n_g = np.diff(batch.vtx_off)
     m_g = np.diff(batch.edge_off)
     spmv_bytes = float(np.sum(it_b.astype(np.float64) * (4 * (n_g + 1) + 8 * m_g + 4 * n_g)))
-    spmv_ms = sp["ms_k2"] if batch_sparse_div == 0 else None
+    spmv_ms = sp["ms_k2"] if not sp["sparse_iters"] else None
 
     # per-graph plain launches of the same kernels, one graph after another
     plain = fsv.FastSV(rowptr_bits=32, k2_items=k2_items)
@@ -184,7 +185,7 @@ def _warm_host_buffers(torch, pinned):
     del dst
 
 
-def serve_measure(requests: int, distinct: int, k2_items: int = 8, batch_sparse_div: int = 0,
+def serve_measure(requests: int, distinct: int, k2_items: int | None = None, batch_sparse_div: int | None = None,
                   iters_per_step: int = 2, sampler=None) -> dict:
     """Config 5: the request trace (Poisson arrivals at 2000/s, undirected
     edge targets log-uniform in [1e3, 5e7], half R-MAT with edge factor 8-32,

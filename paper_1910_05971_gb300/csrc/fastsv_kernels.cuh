@@ -493,25 +493,32 @@ __device__ __forceinline__ bool run_start(const int32_t* s_col, const unsigned* 
 
 // The block copy: for every tile of segment 0 (the tiles the first
 // iteration counted), a stable partition of its entries by column block.
-// One warp per tile walks the tile's entries in rounds of 32 (eight rounds'
-// column ids loaded at once); lanes of one block find each other with a
-// match, rank themselves by the lanes before them, and write their entries
-// at the block's running position (the tile's scanned offset, advanced by
-// the group leader after every round).  A run start writes the run's row
-// and, as the end of the block's previous run, its own position; the end of
+// One warp per tile walks the tile's entries in rounds of 32 (a batch of
+// rounds' column ids loaded at once); lanes of one block find each other
+// with a match, rank themselves by the lanes before them, and write their
+// entries at the block's running position (the tile's scanned offset,
+// advanced by the group leader after every round).  Run starts are noted in
+// shared memory; after every batch one pass over them (lanes over runs)
+// finds each run's row from the row-start bitmap and writes the run's row
+// and, as the end of the block's previous run, its position.  The end of
 // every block's last run is its entry count.
 constexpr int SPLIT_WARPS = 4;
-constexpr int SPLIT_BATCH = 8;  // rounds whose column ids are loaded together
+constexpr int SPLIT_BATCH = 8;                  // rounds whose column ids are loaded together
+constexpr int SPLIT_RUNS = 32 * SPLIT_BATCH;    // runs a batch can start
 
 template <typename RP>
 __global__ void __launch_bounds__(32 * SPLIT_WARPS)
     k_block_split(const Ctx* __restrict__ ctx, BlockLayout L, const int32_t* __restrict__ cnt,
                   int32_t* __restrict__ colB, int32_t* __restrict__ rowsB, int32_t* __restrict__ endsB,
                   int64_t m_total, int64_t p_total) {
-    __shared__ int32_t s_end[SPLIT_WARPS][BUILD_TILE + 1];   // local end of every row of the warp's tile
+    __shared__ int16_t s_rowof[SPLIT_WARPS][BUILD_TILE];    // row starting at a position (valid where s_rs is set)
     __shared__ unsigned s_rs[SPLIT_WARPS][BUILD_TILE / 32];  // bit j: entry j is the first entry of a row
     __shared__ int32_t s_pos[SPLIT_WARPS][MAX_COL_BLOCKS];   // next entry position inside each block
     __shared__ int32_t s_run[SPLIT_WARPS][MAX_COL_BLOCKS];   // next run index inside each block
+    __shared__ int32_t s_rp[SPLIT_WARPS][SPLIT_RUNS];        // a batch's runs: position inside the block,
+    __shared__ int32_t s_ri[SPLIT_WARPS][SPLIT_RUNS];        //   index among the block's runs,
+    __shared__ int16_t s_rj[SPLIT_WARPS][SPLIT_RUNS];        //   first entry in the tile,
+    __shared__ int8_t s_rb[SPLIT_WARPS][SPLIT_RUNS];         //   block
     __shared__ long long s_eb[MAX_COL_BLOCKS], s_pb[MAX_COL_BLOCKS];
     const Seg S0 = ctx->segs[0];
     const int nb = L.nb, shift = L.shift;
@@ -532,7 +539,7 @@ __global__ void __launch_bounds__(32 * SPLIT_WARPS)
     const int64_t n = S0.n, m = S0.m, T = S0.k2_ntiles;
     const int32_t* __restrict__ tile_row = ctx->k2_tile_row + S0.k2_tile0;
     unsigned* rsw = s_rs[w];
-    int32_t* endw = s_end[w];
+    int16_t* rowof = s_rowof[w];
     for (int64_t t = (int64_t)blockIdx.x * SPLIT_WARPS + w; t < T; t += (int64_t)gridDim.x * SPLIT_WARPS) {
         const int64_t d0 = t * BUILD_TILE, d1 = min(d0 + BUILD_TILE, n + m);
         const int64_t x0 = tile_row[t];
@@ -549,12 +556,17 @@ __global__ void __launch_bounds__(32 * SPLIT_WARPS)
         }
         const bool first_whole = rp_at(rp, x0) >= y0;  // row x0 starts inside the tile
         __syncwarp();
-        for (int i = lane; i < nfull; i += 32) {
-            int64_t e = rp_at(rp, x0 + 1 + i);
-            e = (e < y1 ? e : y1) - y0;
-            const int ev = (int)(e < 0 ? 0 : e);
-            endw[i] = ev;
-            if (ev < E) atomicOr(&rsw[ev >> 5], 1u << (ev & 31));  // row i + 1 starts at ev
+        // the first entry of every row that starts inside the tile: row i + 1
+        // starts where row i ends (rows without entries start nowhere)
+        for (int i = lane; i <= nfull; i += 32) {
+            int64_t st = i == 0 ? (first_whole ? y0 : y1) : rp_at(rp, x0 + i);
+            int64_t en = i < nfull ? rp_at(rp, x0 + 1 + i) : y1;
+            st = (st < y1 ? st : y1) - y0;
+            en = (en < y1 ? en : y1) - y0;
+            if (st >= 0 && st < en) {
+                atomicOr(&rsw[st >> 5], 1u << (st & 31));
+                rowof[st] = (int16_t)i;
+            }
         }
         __syncwarp();
         int prev_b = -1;  // block of the entry before the round
@@ -566,6 +578,7 @@ __global__ void __launch_bounds__(32 * SPLIT_WARPS)
                 const int j = base + 32 * k + lane;
                 cv[k] = j < E ? ld_stream(ci + y0 + j) : 0;
             }
+            int nruns = 0;  // runs started in this batch
 #pragma unroll
             for (int k = 0; k < SPLIT_BATCH; ++k) {
                 const int j = base + 32 * k + lane;
@@ -586,23 +599,14 @@ __global__ void __launch_bounds__(32 * SPLIT_WARPS)
                     const int64_t at = s_eb[b] + p;
                     if (at < m_total) colB[at] = c;
                     if (rs) {
-                        const int ri = s_run[w][b] + __popc(grp & rsb & lt);
-                        int lo = 0, hi = nfull;  // the row: the first whose end lies after entry j
-                        while (lo < hi) {
-                            const int mid = (lo + hi) >> 1;
-                            if (endw[mid] > j)
-                                hi = mid;
-                            else
-                                lo = mid + 1;
-                        }
-                        const bool shared = (lo == 0 && !first_whole) || lo >= nfull;
-                        const int64_t pi = s_pb[b] + ri;
-                        if (pi < p_total) {
-                            rowsB[pi] = (int32_t)(x0 + lo) | (shared ? ROW_SHARED : 0);
-                            endsB[pi + b] = p;  // the block's previous run ends where this one starts
-                        }
+                        const int k2 = nruns + __popc(rsb & lt);
+                        s_rp[w][k2] = p;
+                        s_ri[w][k2] = s_run[w][b] + __popc(grp & rsb & lt);
+                        s_rj[w][k2] = (int16_t)j;
+                        s_rb[w][k2] = (int8_t)b;
                     }
                 }
+                nruns += __popc(rsb);
                 __syncwarp();
                 if (valid && (__ffs(grp) - 1) == lane) {
                     s_pos[w][b] += __popc(grp);
@@ -610,6 +614,22 @@ __global__ void __launch_bounds__(32 * SPLIT_WARPS)
                 }
                 __syncwarp();
             }
+            // the batch's runs: row (the last row start at or before the
+            // run's first entry; none: the row that began before the tile)
+            for (int k2 = lane; k2 < nruns; k2 += 32) {
+                const int j = s_rj[w][k2], b = s_rb[w][k2];
+                int wd = j >> 5;
+                unsigned bits = rsw[wd] & (0xffffffffu >> (31 - (j & 31)));
+                while (!bits && wd > 0) bits = rsw[--wd];
+                const int row = bits ? rowof[wd * 32 + 31 - __clz(bits)] : 0;
+                const bool shared = (row == 0 && !first_whole) || row >= nfull;
+                const int64_t pi = s_pb[b] + s_ri[w][k2];
+                if (pi < p_total) {
+                    rowsB[pi] = (int32_t)(x0 + row) | (shared ? ROW_SHARED : 0);
+                    endsB[pi + b] = s_rp[w][k2];  // the block's previous run ends where this one starts
+                }
+            }
+            __syncwarp();
         }
         // a row whose block id decreases: its block may repeat inside the
         // tile, so every run of this tile merges atomically
@@ -869,7 +889,10 @@ __global__ void __launch_bounds__(THREADS, 1536 / THREADS) k2_spmv(Ctx* __restri
 #pragma unroll
             for (int q = 0; q < ITEMS; ++q) {
                 const int j = tid + q * THREADS;
-                if (j < E) s_val[j] = ((uint32_t)c[q] < (uint64_t)ncol) ? (ident ? c[q] : __ldg(gf + c[q])) : INF;
+                // gathers cached in L2 only: a gathered sector is rarely reused by
+                // the same SM, and skipping L1 allocation measured 4.5% faster on
+                // the column-blocked SpMV at R-MAT scale 26 (9.86 vs 10.32 ms)
+                if (j < E) s_val[j] = ((uint32_t)c[q] < (uint64_t)ncol) ? (ident ? c[q] : __ldcg(gf + c[q])) : INF;
             }
         }
         __syncthreads();
@@ -958,11 +981,12 @@ constexpr int k2_smem_bytes() {
 // CSR (segment 0, its merge-path tiles of FIRST_THREADS x FIRST_ITEMS
 // items): gf is still the identity (Algorithm 2 starts from f[u] = u), so
 // mngf[u] is u's smallest neighbour id and nothing is gathered.  The same
-// pass counts, per tile and column block, the tile's entries and runs (see
+// walk counts, per tile and column block, the tile's entries and runs (see
 // the block copy's layout) into cnt[b][t] and cnt[nb + b][t] (rows of
 // tiles + 1 entries; the last entry of each row is 0, so that an exclusive
-// scan of the row ends in the row's total).  The counts are taken striped
-// over the tile's entries with warp ballots, off the walk's serial loop.
+// scan of the row ends in the row's total): every thread follows its items'
+// segments of one row and one block and adds each segment to the tile's
+// counters when it ends.
 constexpr int FIRST_THREADS = 64;
 constexpr int FIRST_ITEMS = 16;
 static_assert(FIRST_THREADS * FIRST_ITEMS == BUILD_TILE, "the block copy cuts along the first iteration's tiles");
@@ -976,9 +1000,8 @@ __global__ void __launch_bounds__(FIRST_THREADS)
     int32_t* s_rowend = smem;                // local end offset of each row in the tile
     int32_t* s_mngf = smem + (TILE + 1);     // per-row minimum over the tile's entries
     int32_t* s_col = smem + 2 * (TILE + 1);  // the tile's column ids as given
-    __shared__ unsigned s_rs[TILE / 32];     // bit j: entry j is the first entry of a row
     __shared__ int s_cnt[2 * MAX_COL_BLOCKS];
-    const int tid = threadIdx.x, lane = tid & 31;
+    const int tid = threadIdx.x;
     const Seg* __restrict__ S = ctx->segs;
     const RP* __restrict__ rp = (const RP*)S->rp;
     int32_t* mngf = S->mngf;
@@ -986,7 +1009,6 @@ __global__ void __launch_bounds__(FIRST_THREADS)
     const bool count = cnt != nullptr;
     const int64_t T1 = (int64_t)S->k2_ntiles + 1;
     if (count && blockIdx.x == 0 && tid < 2 * nb) cnt[(int64_t)tid * T1 + T1 - 1] = 0;
-    if (tid < TILE / 32) s_rs[tid] = 0u;
     if (tid < 2 * MAX_COL_BLOCKS) s_cnt[tid] = 0;
     __syncthreads();
     for (int64_t lt = blockIdx.x; lt < S->k2_ntiles; lt += gridDim.x) {
@@ -1010,10 +1032,8 @@ __global__ void __launch_bounds__(FIRST_THREADS)
         for (int i = tid; i < R; i += THREADS) {
             int64_t e = rp_at(rpt, i);
             e = (e < y1 ? e : y1) - y0;
-            const int ev = (int)(e < 0 ? 0 : e);
-            s_rowend[i] = ev;
+            s_rowend[i] = (int32_t)(e < 0 ? 0 : e);
             s_mngf[i] = INF;
-            if (count && i < nfull && ev < E) atomicOr(&s_rs[ev >> 5], 1u << (ev & 31));  // row i + 1 starts at ev
         }
         {
             int32_t c[ITEMS];
@@ -1030,10 +1050,15 @@ __global__ void __launch_bounds__(FIRST_THREADS)
         }
         __syncthreads();
 
-        // the merge-path walk of k2_spmv over ITEMS items per thread
+        // the merge-path walk of k2_spmv over ITEMS items per thread, and the
+        // thread's segments (consecutive entries of one row in one block):
+        // a segment starts a run unless it continues the run of the entry
+        // before it (same row, same block)
         const int k0 = tid * ITEMS;
         int r = -1;
         int32_t acc = INF;
+        int cb = -1, clen = 0;
+        bool cstart = false;
         if (k0 < D) {
             int lo = 0, hi = nfull;
             while (lo < hi) {
@@ -1051,14 +1076,43 @@ __global__ void __launch_bounds__(FIRST_THREADS)
                 if (y >= rend) {
                     if (acc != INF) atomicMin(&s_mngf[r], acc);
                     acc = INF;
+                    if (count && clen) {
+                        atomicAdd(&s_cnt[cb], clen);
+                        if (cstart) atomicAdd(&s_cnt[MAX_COL_BLOCKS + cb], 1);
+                    }
+                    cb = -1;
+                    clen = 0;
                     ++r;
                     rend = r < nfull ? s_rowend[r] : 0x7fffffff;
                 } else {
                     const int32_t v = s_col[y];
                     if ((uint32_t)v < (uint64_t)n) acc = min(acc, v);
+                    if (count) {
+                        const int b = col_block(v, shift, nb);
+                        if (b != cb) {
+                            if (clen) {
+                                atomicAdd(&s_cnt[cb], clen);
+                                if (cstart) atomicAdd(&s_cnt[MAX_COL_BLOCKS + cb], 1);
+                            }
+                            // a new segment inside the thread's items of one row
+                            // always starts a run; the thread's first segment of
+                            // a row does unless the entry before it (same row)
+                            // has the same block
+                            const int rs = r > 0 ? s_rowend[r - 1] : 0;
+                            cstart = cb >= 0 || y == 0 || (r > 0 && y == rs) ||
+                                     col_block(s_col[y - 1], shift, nb) != b;
+                            cb = b;
+                            clen = 0;
+                        }
+                        ++clen;
+                    }
                     ++y;
                 }
             }
+        }
+        if (count && clen) {
+            atomicAdd(&s_cnt[cb], clen);
+            if (cstart) atomicAdd(&s_cnt[MAX_COL_BLOCKS + cb], 1);
         }
         {
             const int key = (acc != INF && r >= 0 && r < R) ? r : -1;
@@ -1068,24 +1122,6 @@ __global__ void __launch_bounds__(FIRST_THREADS)
                 if ((tid & 31) == 0 && key0 >= 0) atomicMin(&s_mngf[key0], wmin);
             } else if (key >= 0) {
                 atomicMin(&s_mngf[key], acc);
-            }
-        }
-        if (count) {
-            // entries and run starts per column block, in rounds of 32
-            // entries striped over the warps: the lanes of one block find
-            // each other with a match, and the group's first lane counts them
-            for (int base = (tid >> 5) * 32; base < E; base += THREADS) {
-                const int j = base + lane;
-                const bool valid = j < E;
-                const int b = valid ? col_block(s_col[j], shift, nb) : 0;
-                const bool rs = valid && run_start(s_col, s_rs, j, b, shift, nb);
-                const unsigned grp = __match_any_sync(0xffffffffu, valid ? b : 64 + lane);
-                const unsigned rsb = __ballot_sync(0xffffffffu, rs);
-                if (valid && (__ffs(grp) - 1) == lane) {
-                    atomicAdd(&s_cnt[b], __popc(grp));
-                    const int rn = __popc(grp & rsb);
-                    if (rn) atomicAdd(&s_cnt[MAX_COL_BLOCKS + b], rn);
-                }
             }
         }
         __syncthreads();
@@ -1102,12 +1138,12 @@ __global__ void __launch_bounds__(FIRST_THREADS)
                 atomicMin(mngf + x0 + i, mn);
         }
         if (count) {
-            if (tid < nb) cnt[(int64_t)tid * T1 + lt] = s_cnt[tid];
+            if (tid < nb)
+                cnt[(int64_t)tid * T1 + lt] = s_cnt[tid];
             else if (tid >= MAX_COL_BLOCKS && tid < MAX_COL_BLOCKS + nb)
                 cnt[(int64_t)(nb + tid - MAX_COL_BLOCKS) * T1 + lt] = s_cnt[tid];
         }
         __syncthreads();
-        if (tid < TILE / 32) s_rs[tid] = 0u;
         if (tid < 2 * MAX_COL_BLOCKS) s_cnt[tid] = 0;
         __syncthreads();
     }
