@@ -223,12 +223,34 @@ def serve_measure(requests: int, distinct: int, k2_items: int | None = None, bat
     arrivals = tr["t"] - tr["t"][0]
     _warm_host_buffers(torch, pinned)
 
+    from paper_1910_05971_gb300 import _lib
+    from paper_1910_05971_gb300.serve import PoolBackend
+
+    class TimedPool(PoolBackend):
+        """The pool, recording every step's device phases (fastsv_pool_step_times)
+        and the graphs resident when it was issued."""
+
+        def __init__(self, *a, **kw):
+            super().__init__(*a, **kw)
+            self.phases = []
+
+        def step(self, iters):
+            super().step(iters)
+            self._resident = _lib.fastsv_pool_usage(self.h)[1]
+
+        def poll(self):
+            out = super().poll()
+            st, ms = _lib.fastsv_pool_step_times(self.h)
+            self.phases.append((ms[0], ms[1], ms[2], self._resident, len(out[0])))
+            return out
+
     def pool_arm(arr):
-        srv = Server(hbm_budget_bytes=120 << 30, max_slots=1024, iters_per_step=iters_per_step, k2_items=k2_items,
-                     batch_sparse_div=batch_sparse_div)
+        backend = TimedPool(120 << 30, 1024, k2_items=k2_items, batch_sparse_div=batch_sparse_div)
+        srv = Server(backend=backend, iters_per_step=iters_per_step)
         for f in [srv.submit(*graphs[i]) for i in range(min(4, K))]:
             f.result()
         srv.completed.clear()
+        backend.phases.clear()
         launches0 = srv.backend.kernel_launches()
         futs = [None] * R
         start = time.perf_counter()
@@ -248,7 +270,14 @@ def serve_measure(requests: int, distinct: int, k2_items: int | None = None, bat
         done = {id(r.future): r.t_done for r in srv.completed}
         lat = np.array([done[id(futs[i])] - (start + arr[i]) for i in range(R)])
         launches = srv.backend.kernel_launches() - launches0
-        steps = srv.steps
+        ph = np.array(backend.phases, dtype=np.float64).reshape(-1, 5)
+        steps = {"steps": int(len(ph)), "wall_s": end - start,
+                 "device_wait_for_copies_s": float(ph[:, 0].sum() / 1e3),
+                 "device_admit_and_tiles_s": float(ph[:, 1].sum() / 1e3),
+                 "device_iterations_s": float(ph[:, 2].sum() / 1e3),
+                 "resident_graphs_per_step_mean": float(ph[:, 3].mean()) if len(ph) else 0.0,
+                 "resident_graphs_per_step_max": int(ph[:, 3].max()) if len(ph) else 0,
+                 "harvested_per_step_mean": float(ph[:, 4].mean()) if len(ph) else 0.0}
         srv.close()
         return res, R / (end - start), lat, launches, steps
 
@@ -278,7 +307,7 @@ def serve_measure(requests: int, distinct: int, k2_items: int | None = None, bat
     clocks = sampler.stop() if sampler is not None else None
     same = all(np.array_equal(lab, ref[i % K]) and it == plain_its[i] for i, (lab, it) in enumerate(res))
     burst = np.zeros(R)
-    _, cap_gps, cap_lat, _, _ = pool_arm(burst)
+    _, cap_gps, cap_lat, _, cap_steps = pool_arm(burst)
     cap_plain_gps, _, _ = plain_arm(burst)
     out = {
         "workload": f"serve_trace_{R}_arrivals_{K}_graphs", "requests": R, "distinct_graphs": K,
@@ -291,7 +320,8 @@ def serve_measure(requests: int, distinct: int, k2_items: int | None = None, bat
                                   "note": "fastsv_cc_host per request in arrival order (copy in, solve, copy out)"},
         "max_sustainable_rate_per_s": {"pool": cap_gps, "plain": cap_plain_gps,
                                        "how": "every request arriving at once; throughput of the drained queue"},
-        "identical_labels_and_iterations": bool(same), "gpu_launches": int(launches), "steps": steps,
+        "identical_labels_and_iterations": bool(same), "gpu_launches": int(launches),
+        "step_phases": steps, "step_phases_all_at_once": cap_steps,
     }
     if clocks is not None:
         out["clocks"] = clocks
