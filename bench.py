@@ -273,6 +273,15 @@ def main():
     peaks, peak_src = measured_peaks()
     peak = float(peaks["hbm_gbs"])
     k2_gbs = k2_bytes / (k2_avg_ms * 1e-3) / 1e9
+    # one full iteration on the counted model r(n+1) + 8m + 44n (SpMV, the
+    # three hooks, grandparents + termination + snapshot)
+    iter_bytes = r * (n + 1) + 8 * m + 44 * n
+    iter_ms = k2_avg_ms + hook_avg_ms + k3_avg_ms
+    per_iter = {"algorithmic_bytes": iter_bytes, "ms": iter_ms,
+                "achieved": iter_bytes / (iter_ms * 1e-3) / 1e9,
+                "frac": iter_bytes / (iter_ms * 1e-3) / 1e9 / peak,
+                "frac_of_nominal_8000": iter_bytes / (iter_ms * 1e-3) / 1e9 / 8000.0,
+                "model": "r(n+1) + 8m + 44n over k2_spmv + k2_hook + k3_grandparent averages"}
     traffic = profiled_traffic(args.workload)
 
     # ---- end to end through the host-buffer entry point ----
@@ -370,6 +379,7 @@ def main():
                                             "achieved": k3_bytes / (k3_avg_ms * 1e-3) / 1e9},
                          "k2_hook": {"algorithmic_bytes_per_launch": hook_bytes, "avg_launch_ms": hook_avg_ms,
                                      "achieved": hook_bytes / (hook_avg_ms * 1e-3) / 1e9},
+                         "per_iteration": per_iter,
                          "dense_iterations_per_solve": dense_sum / args.steps,
                          "sparse_iterations_per_solve": (it_sum - dense_sum) / args.steps,
                          "averaged_dense_launches_per_solve": t_dense / args.steps},
