@@ -117,7 +117,7 @@ typedef struct {
                               on 4096 ER graphs the frontier bookkeeping cost more than the pushes saved
                               (139k graphs/s off, 116k at 4 to 32, 101k at 2) */
     int32_t col_block_mib; /* automatic column blocking (col_blocks = 0): MiB of the grandparent vector per
-                              block (default 32, about a quarter of the L2) */
+                              block (default 64, about half of the L2) */
     int32_t pool_wait_copies; /* pools: 0 (default) = a graph joins the first step after its copies to the
                               device have landed (copies overlap iterations); 1 = every step waits for the
                               copies of all graphs admitted before it, so a graph added before a step
@@ -202,7 +202,10 @@ fastsv_status fastsv_cc(fastsv_t h, int64_t n, const void* row_ptr, const int32_
  * fastsv_cc from host buffers: copies row_ptr and col_idx to handle-owned
  * device memory, solves, and copies the labels back, all on `stream`, and
  * returns when labels_host is filled (synchronises).  Host pointers; pinned
- * memory recommended.  Same sizes and layout as fastsv_cc.
+ * memory recommended.  Same sizes and layout as fastsv_cc.  For a
+ * column-blocked graph (without validation) col_idx is copied in chunks on a
+ * stream of the handle's own, and the first iteration works on every chunk
+ * once it has landed; fastsv_get_stats' ms_total then includes the copy.
  */
 fastsv_status fastsv_cc_host(fastsv_t h, int64_t n, const void* row_ptr_host, const int32_t* col_idx_host,
                              int32_t* labels_host, void* stream);

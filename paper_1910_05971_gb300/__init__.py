@@ -72,7 +72,7 @@ class FastSV:
                  validate: int = 0, use_graph: bool = True, k2_items: int | None = None, grid_ctas_per_sm: int = 0,
                  timing: bool = True, fail_alloc_after: int = 0, col_blocks: int | None = None,
                  k2_threads: int | None = None, sparse_div: int | None = None, variant: int = 0,
-                 batch_sparse_div: int | None = None, col_block_mib: int = 32, pool_wait_copies: bool = False,
+                 batch_sparse_div: int | None = None, col_block_mib: int = 64, pool_wait_copies: bool = False,
                  tune_cache: str | None = "default"):
         _torch()
         o = fastsv_default_options()

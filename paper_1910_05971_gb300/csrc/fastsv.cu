@@ -552,13 +552,13 @@ static int choose_col_blocks(const fastsv_ctx* h, int64_t n, int64_t m) {
     if (nb <= 0) {
         // Automatic: block when the gathered vector (4n bytes) is at least
         // 1.5x the L2 and the graph is dense enough (m >= 8n), one block per
-        // col_block_mib MiB of the gathered vector (default 32: measured on
-        // GB300 at R-MAT scale 26, 8 blocks solve in 56.2 ms, 4 in 56.8, 16 in
-        // 63.8 (the copy's run lists grow with the block count), unblocked
+        // col_block_mib MiB of the gathered vector (default 64: measured on
+        // GB300 at R-MAT scale 26, 4 blocks solve in 51.4 ms, 8 in 52.5, 16 in
+        // 59.4 (the copy's run lists grow with the block count), unblocked
         // in 70.0).
         const int64_t l2 = h->l2_bytes > 0 ? h->l2_bytes : (int64_t)129 << 20;
         if (m < 8 * n || 2 * (4 * n) < 3 * l2) return 1;
-        const int64_t mib = h->opt.col_block_mib > 0 ? h->opt.col_block_mib : 32;
+        const int64_t mib = h->opt.col_block_mib > 0 ? h->opt.col_block_mib : 64;
         const int64_t slice = mib << 20;
         const int64_t want = (4 * n + slice - 1) / slice;
         return (int)(want < 2 ? 2 : (want < MAX_COL_BLOCKS ? want : MAX_COL_BLOCKS));
@@ -620,7 +620,27 @@ static fastsv_status ensure_run_workspace(fastsv_ctx* h, int64_t runs, int nb) {
 // (k2_first) gathers nothing, so the per-tile merge-path search is most of
 // its work: 64 threads x 16 items spend one search on 16 items.  It also
 // counts every tile's entries and runs per column block for the block copy.
-static fastsv_status first_iteration_unblocked(fastsv_ctx* h, int rp64, int nb, int shift, cudaStream_t s) {
+// col_idx of a fastsv_cc_host call still in host memory: the first iteration
+// of a column-blocked solve reads it chunk by chunk as the copies land
+struct HostFeed {
+    const int32_t* ci_host;  // source
+    int32_t* ci_dev;         // destination (the handle's device copy)
+};
+constexpr int FEED_CHUNKS = 8;
+
+static fastsv_status ensure_feed(fastsv_ctx* h) {
+    if (!h->feed_stream) FSV_CUDA(h, cudaStreamCreateWithFlags(&h->feed_stream, cudaStreamNonBlocking));
+    for (int i = 0; i <= FEED_CHUNKS; ++i)
+        if (!h->feed_ev[i]) FSV_CUDA(h, cudaEventCreateWithFlags(&h->feed_ev[i], cudaEventDisableTiming));
+    if (!h->d_feed_tiles) {
+        fastsv_status st = dev_alloc(h, (void**)&h->d_feed_tiles, sizeof(int64_t) * (MAX_FEED_CHUNKS + 1));
+        if (st != FASTSV_OK) return st;
+    }
+    return FASTSV_OK;
+}
+
+static fastsv_status first_iteration_unblocked(fastsv_ctx* h, int rp64, int nb, int shift, int64_t m,
+                                               const HostFeed* feed, cudaStream_t s) {
     IterKernels K;
     fastsv_status st = iter_kernels(h, rp64, rp64, 8, &K);
     if (st != FASTSV_OK) return st;
@@ -634,14 +654,47 @@ static fastsv_status first_iteration_unblocked(fastsv_ctx* h, int rp64, int nb, 
     cudaGraphConditionalHandle none = 0;
     int no_cond = 0;
     void* a_begin[] = {(void*)&ctx, (void*)&none, (void*)&no_cond};
-    void* a_spmv[] = {(void*)&ctx, (void*)&cnt, (void*)&nb, (void*)&shift};
     void* a_ctx[] = {(void*)&ctx};
     void* a_k3[] = {(void*)&ctx, (void*)&none, (void*)&no_cond};
     FSV_CUDA(h, cudaLaunchKernel((const void*)k_iter_begin, dim3(K.vtx_grid), dim3(256), a_begin, 0, s));
-    FSV_CUDA(h, cudaLaunchKernel(spmv, dim3(grid), dim3(FIRST_THREADS), a_spmv, smem, s));
+    h->pending_fixed_launches += 1;
+    if (!feed) {
+        const int64_t* range = nullptr;
+        int chunk = 0;
+        void* a_spmv[] = {(void*)&ctx, (void*)&cnt, (void*)&nb, (void*)&shift, (void*)&range, (void*)&chunk};
+        FSV_CUDA(h, cudaLaunchKernel(spmv, dim3(grid), dim3(FIRST_THREADS), a_spmv, smem, s));
+        h->pending_fixed_launches += 1;
+    } else {
+        // col_idx arrives in FEED_CHUNKS copies on the feed stream (after
+        // everything enqueued on s so far); every chunk's tiles run as soon as
+        // their entries have landed
+        if ((st = ensure_feed(h)) != FASTSV_OK) return st;
+        FeedBounds fb;
+        memset(&fb, 0, sizeof(fb));
+        fb.chunks = FEED_CHUNKS;
+        for (int c = 0; c <= FEED_CHUNKS; ++c) fb.b[c] = m * c / FEED_CHUNKS;
+        k_feed_tiles<<<1, 32, 0, s>>>(ctx, fb, h->d_feed_tiles);
+        FSV_CUDA(h, cudaEventRecord(h->feed_ev[0], s));
+        FSV_CUDA(h, cudaStreamWaitEvent(h->feed_stream, h->feed_ev[0], 0));
+        for (int c = 0; c < FEED_CHUNKS; ++c) {
+            const int64_t e0 = fb.b[c], e1 = fb.b[c + 1];
+            if (e1 > e0)
+                FSV_CUDA(h, cudaMemcpyAsync(feed->ci_dev + e0, feed->ci_host + e0, (size_t)(e1 - e0) * 4,
+                                            cudaMemcpyHostToDevice, h->feed_stream));
+            FSV_CUDA(h, cudaEventRecord(h->feed_ev[1 + c], h->feed_stream));
+        }
+        const int64_t* range = h->d_feed_tiles;
+        for (int c = 0; c < FEED_CHUNKS; ++c) {
+            FSV_CUDA(h, cudaStreamWaitEvent(s, h->feed_ev[1 + c], 0));
+            int chunk = c;
+            void* a_spmv[] = {(void*)&ctx, (void*)&cnt, (void*)&nb, (void*)&shift, (void*)&range, (void*)&chunk};
+            FSV_CUDA(h, cudaLaunchKernel(spmv, dim3(grid), dim3(FIRST_THREADS), a_spmv, smem, s));
+        }
+        h->pending_fixed_launches += 1 + FEED_CHUNKS;
+    }
     FSV_CUDA(h, cudaLaunchKernel(K.hook, dim3(K.vtx_grid), dim3(K3_THREADS), a_ctx, 0, s));
     FSV_CUDA(h, cudaLaunchKernel(K.k3, dim3(K.vtx_grid), dim3(K3_THREADS), a_k3, 0, s));
-    h->pending_fixed_launches += 4;
+    h->pending_fixed_launches += 2;
     return FASTSV_OK;
 }
 
@@ -681,9 +734,9 @@ static fastsv_status build_blocks(fastsv_ctx* h, int nb, int shift, int64_t tile
     h->last_runs = runs;
     Ctx* ctx = h->d_ctx;
     int per_sm = 0;
-    FSV_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k_block_split<RP>, BUILD_THREADS, 0));
+    FSV_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k_block_split<RP>, SPLIT_THREADS, 0));
     const int grid = (per_sm > 0 ? per_sm : 1) * h->num_sms;
-    k_block_split<RP><<<grid, BUILD_THREADS, 0, s>>>(ctx, L, h->d_counts, h->d_colB, h->d_rowsB, h->d_endsB, m, runs);
+    k_block_split<RP><<<grid, SPLIT_THREADS, 0, s>>>(ctx, L, h->d_counts, h->d_colB, h->d_rowsB, h->d_endsB, m, runs);
     k_setup_blocks<<<1, 1, 0, s>>>(ctx, L, h->d_colB, h->d_rowsB, h->d_endsB, tile);
     k_scan_tiles<<<1, 1024, 0, s>>>(ctx);
     k_partition<int32_t><<<setup_grid(h), 256, 0, s>>>(ctx);
@@ -693,7 +746,7 @@ static fastsv_status build_blocks(fastsv_ctx* h, int nb, int shift, int64_t tile
 }
 
 static fastsv_status solve_single(fastsv_ctx* h, int64_t n, int64_t m, const void* rp, const int32_t* ci,
-                                  int32_t* labels, cudaStream_t s) {
+                                  int32_t* labels, cudaStream_t s, const int32_t* ci_host = nullptr) {
     const int rp64 = h->opt.rowptr_bits == 64;
     const int items = k2_items(h);
     // the ablation variants sv1..sv4 and the asynchronous mode run unblocked
@@ -717,6 +770,12 @@ static fastsv_status solve_single(fastsv_ctx* h, int64_t n, int64_t m, const voi
     fastsv_status st = ensure_workspace(h, n, t2 > t2b ? t2 : t2b, t3, 1 + nb_eff);
     if (st != FASTSV_OK) return st;
     if (nb_eff > 1 && (st = ensure_block_workspace(h, nb_eff, t2, m)) != FASTSV_OK) return st;
+    // col_idx still in host memory: a blocked solve without validation copies
+    // it chunk by chunk under its first iteration; any other copies it now
+    HostFeed feed{ci_host, const_cast<int32_t*>(ci)};
+    const bool fed = ci_host && m > 0 && nb_eff > 1 && !h->opt.validate;
+    if (ci_host && m > 0 && !fed)
+        FSV_CUDA(h, cudaMemcpyAsync(const_cast<int32_t*>(ci), ci_host, (size_t)m * 4, cudaMemcpyHostToDevice, s));
     h->pending_fixed_launches = 0;
     h->ms_k2 = h->ms_k3 = h->ms_push = h->ms_hook = 0.f;
     h->dense_iters = 0;
@@ -754,7 +813,8 @@ static fastsv_status solve_single(fastsv_ctx* h, int64_t n, int64_t m, const voi
         // block copy.
         k_init_state<<<setup_grid(h), 256, 0, s>>>(h->d_ctx);
         h->pending_fixed_launches += 1;
-        if ((st = first_iteration_unblocked(h, rp64, nb_eff, shift, s)) != FASTSV_OK) return st;
+        if ((st = first_iteration_unblocked(h, rp64, nb_eff, shift, m, fed ? &feed : nullptr, s)) != FASTSV_OK)
+            return st;
         // split the entries into column blocks of compressed rows
         st = rp64 ? build_blocks<int64_t>(h, nb_eff, shift, t2, m, (int32_t)tile, s)
                   : build_blocks<int32_t>(h, nb_eff, shift, t2, m, (int32_t)tile, s);
@@ -804,7 +864,7 @@ void fastsv_default_options(fastsv_options* o) {
     o->col_blocks = 0;
     o->k2_threads = 256;
     o->sparse_div = 2;
-    o->col_block_mib = 32;
+    o->col_block_mib = 64;
     o->tune_cache = nullptr;
 }
 
@@ -896,6 +956,10 @@ fastsv_status fastsv_destroy(fastsv_t h) {
     dev_free((void**)&h->d_rowsB);
     dev_free((void**)&h->d_endsB);
     dev_free((void**)&h->d_build_scalars);
+    dev_free((void**)&h->d_feed_tiles);
+    if (h->feed_stream) cudaStreamDestroy(h->feed_stream);
+    for (cudaEvent_t& ev : h->feed_ev)
+        if (ev) cudaEventDestroy(ev);
     dev_free(&h->d_rp_copy);
     dev_free((void**)&h->d_ci_copy);
     dev_free((void**)&h->d_lab_copy);
@@ -970,8 +1034,11 @@ fastsv_status fastsv_cc_host(fastsv_t h, int64_t n, const void* row_ptr_host, co
         return st;
     if ((st = ensure_copy(h, (void**)&h->d_lab_copy, &h->cap_lab_copy, (size_t)n * 4)) != FASTSV_OK) return st;
     FSV_CUDA(h, cudaMemcpyAsync(h->d_rp_copy, row_ptr_host, (size_t)(n + 1) * w, cudaMemcpyHostToDevice, s));
-    if (m > 0) FSV_CUDA(h, cudaMemcpyAsync(h->d_ci_copy, col_idx_host, (size_t)m * 4, cudaMemcpyHostToDevice, s));
-    if ((st = solve_single(h, n, m, h->d_rp_copy, h->d_ci_copy, h->d_lab_copy, s)) != FASTSV_OK) return st;
+    // col_idx is copied by the solve: for a column-blocked graph in chunks
+    // that overlap its first iteration
+    if ((st = solve_single(h, n, m, h->d_rp_copy, h->d_ci_copy, h->d_lab_copy, s, m > 0 ? col_idx_host : nullptr)) !=
+        FASTSV_OK)
+        return st;
     FSV_CUDA(h, cudaMemcpyAsync(labels_host, h->d_lab_copy, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
     FSV_CUDA(h, cudaStreamSynchronize(s));
     fastsv_stats tmp;

@@ -81,6 +81,12 @@ struct fastsv_ctx {
     int64_t last_runs = 0;
     int last_col_blocks = 1;
 
+    // the host-buffer entry point's copy of col_idx in chunks, overlapping the
+    // first iteration of a column-blocked solve
+    cudaStream_t feed_stream = nullptr;
+    cudaEvent_t feed_ev[17] = {};        // [0]: the call's stream reached the copies; [1 + c]: chunk c landed
+    int64_t* d_feed_tiles = nullptr;     // first-iteration tile range of every chunk
+
     // device copies for the host-buffer entry point
     void* d_rp_copy = nullptr;
     size_t cap_rp_copy = 0;

@@ -503,6 +503,7 @@ __device__ __forceinline__ bool run_start(const int32_t* s_col, const unsigned* 
 // and, as the end of the block's previous run, its position.  The end of
 // every block's last run is its entry count.
 constexpr int SPLIT_WARPS = 4;
+constexpr int SPLIT_THREADS = 32 * SPLIT_WARPS;
 constexpr int SPLIT_BATCH = 8;                  // rounds whose column ids are loaded together
 constexpr int SPLIT_RUNS = 32 * SPLIT_BATCH;    // runs a batch can start
 
@@ -994,7 +995,8 @@ static_assert(FIRST_THREADS >= 2 * MAX_COL_BLOCKS, "one thread per count of a ti
 
 template <typename RP>
 __global__ void __launch_bounds__(FIRST_THREADS)
-    k2_first(Ctx* __restrict__ ctx, int32_t* __restrict__ cnt, int nb, int shift) {
+    k2_first(Ctx* __restrict__ ctx, int32_t* __restrict__ cnt, int nb, int shift, const int64_t* __restrict__ range,
+             int chunk) {
     constexpr int THREADS = FIRST_THREADS, ITEMS = FIRST_ITEMS, TILE = THREADS * ITEMS;
     extern __shared__ int32_t smem[];
     int32_t* s_rowend = smem;                // local end offset of each row in the tile
@@ -1008,10 +1010,12 @@ __global__ void __launch_bounds__(FIRST_THREADS)
     const int64_t n = S->n, m = S->m;
     const bool count = cnt != nullptr;
     const int64_t T1 = (int64_t)S->k2_ntiles + 1;
-    if (count && blockIdx.x == 0 && tid < 2 * nb) cnt[(int64_t)tid * T1 + T1 - 1] = 0;
+    // range (may be null): this launch takes the tiles [range[chunk], range[chunk + 1])
+    const int64_t lt0 = range ? range[chunk] : 0, lt1 = range ? range[chunk + 1] : S->k2_ntiles;
+    if (count && blockIdx.x == 0 && chunk == 0 && tid < 2 * nb) cnt[(int64_t)tid * T1 + T1 - 1] = 0;
     if (tid < 2 * MAX_COL_BLOCKS) s_cnt[tid] = 0;
     __syncthreads();
-    for (int64_t lt = blockIdx.x; lt < S->k2_ntiles; lt += gridDim.x) {
+    for (int64_t lt = lt0 + blockIdx.x; lt < lt1; lt += gridDim.x) {
         const int64_t t = S->k2_tile0 + lt;
         const int64_t d0 = lt * TILE;
         const int64_t d1 = min(d0 + (int64_t)TILE, n + m);
@@ -1147,6 +1151,41 @@ __global__ void __launch_bounds__(FIRST_THREADS)
         if (tid < 2 * MAX_COL_BLOCKS) s_cnt[tid] = 0;
         __syncthreads();
     }
+}
+
+// Entry bounds of the chunks in which col_idx arrives from host memory, and
+// for each bound the number of first-iteration tiles whose entries all lie
+// below it (tiles end at non-decreasing entry positions, so each count is a
+// binary search): chunk c's launch of k2_first takes tiles [out[c], out[c+1]).
+constexpr int MAX_FEED_CHUNKS = 16;
+struct FeedBounds {
+    int64_t b[MAX_FEED_CHUNKS + 1];  // b[c + 1]: entries copied once chunk c has landed
+    int32_t chunks;
+};
+
+__global__ void k_feed_tiles(const Ctx* __restrict__ ctx, FeedBounds fb, int64_t* __restrict__ out) {
+    const Seg& S = ctx->segs[0];
+    const int64_t T = S.k2_ntiles, n = S.n, m = S.m, tile = ctx->k2_tile;
+    const int32_t* tile_row = ctx->k2_tile_row + S.k2_tile0;
+    const int c = threadIdx.x;
+    if (c > fb.chunks) return;
+    if (c == 0 || c == fb.chunks) {
+        out[c] = c == 0 ? 0 : T;
+        return;
+    }
+    // tiles t < lo end at or below the bound: y1(t) = min((t + 1) tile, n + m) - x1(t)
+    const int64_t bound = fb.b[c];
+    int64_t lo = 0, hi = T;
+    while (lo < hi) {
+        const int64_t t = (lo + hi) >> 1;
+        const int64_t d1 = min((t + 1) * tile, n + m);
+        const int64_t x1 = t + 1 < T ? (int64_t)tile_row[t + 1] : n;
+        if (d1 - x1 <= bound)
+            lo = t + 1;
+        else
+            hi = t;
+    }
+    out[c] = lo;
 }
 
 __host__ __device__ constexpr int k2_first_smem() { return (3 * (FIRST_THREADS * FIRST_ITEMS) + 2) * (int)sizeof(int32_t); }

@@ -23,6 +23,9 @@ def test_traffic_follows_workload_and_kernel_source(monkeypatch):
     wl = rows["workload"]
     if rows["kernel_source_sha256_16"] == bench.kernel_source_hash():
         assert bench.profiled_traffic(wl) == float(rows["dram_bytes_per_launch"])
+        # taken at one column-block count: another count drops it
+        assert bench.profiled_traffic(wl, int(rows["col_blocks"])) == float(rows["dram_bytes_per_launch"])
+        assert bench.profiled_traffic(wl, int(rows["col_blocks"]) + 1) is None
     else:
         assert bench.profiled_traffic(wl) is None
     assert bench.profiled_traffic("rmat_s16") is None

@@ -227,6 +227,28 @@ def test_host_buffer_entry_point():
         assert s.stats()["iterations"] == it
 
 
+@pytest.mark.parametrize("col_blocks", [2, 4, 16])
+def test_host_buffer_entry_point_column_blocked(col_blocks):
+    """fastsv_cc_host on a column-blocked solve copies col_idx in chunks that
+    overlap the first iteration (each chunk's tiles run once their entries
+    have landed): labels, iterations and the per-iteration trace must still
+    be Algorithm 2's, on repeated calls into the same device buffers."""
+    import paper_1910_05971_gb300 as fsv
+    torch = pytest.importorskip("torch")
+    for seed in (8, 9):
+        rp, ci = graphgen.rmat(13, 16, seed=seed, permute=True)
+        f, it, _, ch = oracle.fastsv(rp, ci, form="omp")
+        rp_h = torch.from_numpy(rp).pin_memory()
+        ci_h = torch.from_numpy(ci).pin_memory()
+        with fsv.FastSV(col_blocks=col_blocks) as s:
+            for _ in range(2):
+                lab = s.cc_host(rp_h, ci_h)
+                st = s.stats()
+                assert st["col_blocks"] > 1
+                assert np.array_equal(lab.numpy(), f) and st["iterations"] == it
+                assert st["changed_per_iter"] == ch.tolist()
+
+
 def test_non_default_stream_and_launch_count():
     import paper_1910_05971_gb300 as fsv
     torch = pytest.importorskip("torch")
