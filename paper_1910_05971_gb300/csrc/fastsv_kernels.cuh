@@ -430,67 +430,6 @@ struct BlockLayout {
     int64_t pbase[MAX_COL_BLOCKS + 1];
 };
 
-// per tile of the graph's own merge-path partition (segment 0): row ends,
-// column ids, row count R, entry count E; returns false for an empty tile
-template <typename RP, int ITEMS = BUILD_ITEMS>
-__device__ __forceinline__ bool load_tile(const Seg& S, int64_t t, int64_t tile, const int32_t* tile_row,
-                                          int32_t* s_rowend, int32_t* s_col, int64_t& x0, int& nfull, int& R,
-                                          int& E, int& D) {
-    const RP* rp = (const RP*)S.rp;
-    const int64_t n = S.n, m = S.m;
-    const int64_t lt = t - S.k2_tile0;
-    const int64_t d0 = lt * tile, d1 = min(d0 + tile, n + m);
-    x0 = tile_row[t];
-    const int64_t x1 = (lt + 1 < S.k2_ntiles) ? (int64_t)tile_row[t + 1] : n;
-    if (x1 < x0) return false;
-    const int64_t y0 = d0 - x0, y1 = d1 - x1;
-    nfull = (int)(x1 - x0);
-    R = nfull + (x1 < n ? 1 : 0);
-    E = (int)(y1 - y0);
-    D = (int)(d1 - d0);
-    // loads first, stores after (clamped addresses); ITEMS bounds tile / blockDim
-    const int per = (int)(tile / blockDim.x);
-    int64_t e[ITEMS + 1];
-    int32_t c[ITEMS];
-#pragma unroll
-    for (int q = 0; q <= ITEMS; ++q) {
-        if (q > per) break;
-        const int i = threadIdx.x + q * blockDim.x;
-        int64_t row = x0 + (i < R ? i : 0) + 1;
-        e[q] = rp_at(rp, row < n ? row : n);
-    }
-#pragma unroll
-    for (int q = 0; q < ITEMS; ++q) {
-        if (q >= per) break;
-        const int j = threadIdx.x + q * blockDim.x;
-        int64_t pos = y0 + (j < E ? j : 0);
-        c[q] = ld_stream(S.ci + (pos < m ? pos : m - 1));
-    }
-#pragma unroll
-    for (int q = 0; q <= ITEMS; ++q) {
-        if (q > per) break;
-        const int i = threadIdx.x + q * blockDim.x;
-        if (i < R) {
-            int64_t v = (e[q] < y1 ? e[q] : y1) - y0;
-            s_rowend[i] = (int32_t)(v < 0 ? 0 : v);
-        }
-    }
-#pragma unroll
-    for (int q = 0; q < ITEMS; ++q) {
-        if (q >= per) break;
-        const int j = threadIdx.x + q * blockDim.x;
-        if (j < E) s_col[j] = c[q];
-    }
-    return true;
-}
-
-// is tile entry j the first of a run (the tile's first entry, a row's first
-// entry, or a change of column block inside a row)?  s_rs marks the first
-// entry of every row that starts inside the tile.
-__device__ __forceinline__ bool run_start(const int32_t* s_col, const unsigned* s_rs, int j, int b, int shift, int nb) {
-    return j == 0 || ((s_rs[j >> 5] >> (j & 31)) & 1u) || col_block(s_col[j - 1], shift, nb) != b;
-}
-
 // The block copy: for every tile of segment 0 (the tiles the first
 // iteration counted), a stable partition of its entries by column block.
 // One warp per tile walks the tile's entries in rounds of 32 (a batch of
