@@ -484,7 +484,9 @@ __global__ void __launch_bounds__(32 * SPLIT_WARPS)
         const int64_t d0 = t * BUILD_TILE, d1 = min(d0 + BUILD_TILE, n + m);
         const int64_t x0 = tile_row[t];
         const int64_t x1 = t + 1 < T ? (int64_t)tile_row[t + 1] : n;
-        if (x1 < x0) continue;  // only possible for a malformed row_ptr
+        // a malformed row_ptr (validation off) can give tiles whose rows run
+        // backwards or outnumber their items: skip them, so no index leaves the tile
+        if (x1 < x0 || x1 - x0 > d1 - d0) continue;
         const int64_t y0 = d0 - x0, y1 = d1 - x1;
         const int nfull = (int)(x1 - x0);
         const int E = (int)(y1 - y0);
@@ -801,7 +803,9 @@ __global__ void __launch_bounds__(THREADS, 1536 / THREADS) k2_spmv(Ctx* __restri
         const int64_t d1 = min(d0 + (int64_t)TILE, n + m);
         const int64_t x0 = xr0;
         const int64_t x1 = (lt + 1 < S->k2_ntiles) ? (int64_t)xr1 : n;
-        if (x1 < x0) continue;  // only possible for a malformed row_ptr
+        // a malformed row_ptr (validation off) can give tiles whose rows run
+        // backwards or outnumber their items: skip them, so no index leaves the tile
+        if (x1 < x0 || x1 - x0 > d1 - d0) continue;
         const int64_t y0 = d0 - x0, y1 = d1 - x1;
         const int nfull = (int)(x1 - x0);            // rows whose end lies in this tile
         const int R = nfull + (x1 < n ? 1 : 0);       // plus the row still open at the tile end
@@ -960,7 +964,7 @@ __global__ void __launch_bounds__(FIRST_THREADS)
         const int64_t d1 = min(d0 + (int64_t)TILE, n + m);
         const int64_t x0 = ctx->k2_tile_row[t];
         const int64_t x1 = (lt + 1 < S->k2_ntiles) ? (int64_t)ctx->k2_tile_row[t + 1] : n;
-        if (x1 < x0) {  // only possible for a malformed row_ptr
+        if (x1 < x0 || x1 - x0 > d1 - d0) {  // only possible for a malformed row_ptr
             if (count && tid < 2 * nb) cnt[(int64_t)tid * T1 + lt] = 0;
             continue;
         }

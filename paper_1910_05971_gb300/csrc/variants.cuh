@@ -152,7 +152,9 @@ __global__ void __launch_bounds__(THREADS, 5) k_async(Ctx* __restrict__ ctx) {
         const int64_t d1 = min(d0 + (int64_t)TILE, n + m);
         const int64_t x0 = tile_row[t];
         const int64_t x1 = (t + 1 < T) ? (int64_t)tile_row[t + 1] : n;
-        if (x1 < x0) continue;  // only possible for a malformed row_ptr
+        // a malformed row_ptr (validation off) can give tiles whose rows run
+        // backwards or outnumber their items: skip them, so no index leaves the tile
+        if (x1 < x0 || x1 - x0 > d1 - d0) continue;
         const int64_t y0 = d0 - x0, y1 = d1 - x1;
         const int nfull = (int)(x1 - x0);
         const int R = nfull + (x1 < n ? 1 : 0);
