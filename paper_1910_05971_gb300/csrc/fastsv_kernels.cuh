@@ -63,6 +63,14 @@ __device__ __forceinline__ int64_t rp_at(const RP* rp, int64_t i) { return (int6
 // number of rows i in [0, n) whose merge-path row-end position rp[i+1] + i is
 // < d (rows fully consumed before diagonal d); Merrill & Garland's merge-path
 // search specialised to "row ends vs. entry indices".
+// Position of staged entry j in shared memory: one padding word after every
+// ITEMS entries.  In a merge-path walk the threads of a warp read entries
+// about ITEMS words apart, which puts gcd(ITEMS, 32) lanes on one bank (8
+// for ITEMS = 8); padded, the stride is ITEMS + 1, odd, and every lane reads
+// its own bank.
+template <int ITEMS>
+__device__ __forceinline__ int stage_at(int j) { return j + j / ITEMS; }
+
 template <typename RP>
 __device__ __forceinline__ int64_t merge_path_rows(const RP* rp, int64_t n, int64_t m, int64_t d) {
     int64_t lo = d > m ? d - m : 0;
@@ -748,7 +756,7 @@ __global__ void __launch_bounds__(THREADS, 1536 / THREADS) k2_spmv(Ctx* __restri
     extern __shared__ int32_t smem[];
     int32_t* s_rowend = smem;                 // local end offset of each row in the tile
     int32_t* s_mngf = smem + (TILE + 1);      // per-row minimum over the tile's entries
-    int32_t* s_val = smem + 2 * (TILE + 1);   // gf[col_idx[e]] for the tile's entries
+    int32_t* s_val = smem + 2 * (TILE + 1);   // gf[col_idx[e]] for the tile's entries (at stage_at)
     const int tid = threadIdx.x;
     const int32_t* __restrict__ tile_seg = ctx->k2_tile_seg;
     const int32_t* __restrict__ tile_row = ctx->k2_tile_row;
@@ -830,13 +838,17 @@ __global__ void __launch_bounds__(THREADS, 1536 / THREADS) k2_spmv(Ctx* __restri
                 const int j = tid + q * THREADS;
                 c[q] = j < E ? ld_stream(cit + j) : -1;
             }
+            // entry tid + q THREADS sits at stage_at(tid) + q (THREADS + THREADS / ITEMS)
+            const int sb = stage_at<ITEMS>(tid);
 #pragma unroll
             for (int q = 0; q < ITEMS; ++q) {
                 const int j = tid + q * THREADS;
                 // gathers cached in L2 only: a gathered sector is rarely reused by
                 // the same SM, and skipping L1 allocation measured 4.5% faster on
                 // the column-blocked SpMV at R-MAT scale 26 (9.86 vs 10.32 ms)
-                if (j < E) s_val[j] = ((uint32_t)c[q] < (uint64_t)ncol) ? (ident ? c[q] : __ldcg(gf + c[q])) : INF;
+                if (j < E)
+                    s_val[sb + q * (THREADS + THREADS / ITEMS)] =
+                        ((uint32_t)c[q] < (uint64_t)ncol) ? (ident ? c[q] : __ldcg(gf + c[q])) : INF;
             }
         }
         __syncthreads();
@@ -869,7 +881,7 @@ __global__ void __launch_bounds__(THREADS, 1536 / THREADS) k2_spmv(Ctx* __restri
                     ++r;
                     rend = r < nfull ? s_rowend[r] : 0x7fffffff;
                 } else {
-                    acc = min(acc, s_val[y]);
+                    acc = min(acc, s_val[stage_at<ITEMS>(y)]);
                     ++y;
                 }
             }
@@ -918,7 +930,7 @@ __global__ void __launch_bounds__(THREADS, 1536 / THREADS) k2_spmv(Ctx* __restri
 
 template <int THREADS, int ITEMS>
 constexpr int k2_smem_bytes() {
-    return (2 * (THREADS * ITEMS + 1) + THREADS * ITEMS) * (int)sizeof(int32_t);
+    return (2 * (THREADS * ITEMS + 1) + THREADS * ITEMS + THREADS) * (int)sizeof(int32_t);
 }
 
 // a1 in the first iteration of a column-blocked solve, on the graph's own
@@ -944,7 +956,7 @@ __global__ void __launch_bounds__(FIRST_THREADS)
     extern __shared__ int32_t smem[];
     int32_t* s_rowend = smem;                // local end offset of each row in the tile
     int32_t* s_mngf = smem + (TILE + 1);     // per-row minimum over the tile's entries
-    int32_t* s_col = smem + 2 * (TILE + 1);  // the tile's column ids as given
+    int32_t* s_col = smem + 2 * (TILE + 1);  // the tile's column ids as given (at stage_at)
     __shared__ int s_cnt[2 * MAX_COL_BLOCKS];
     const int tid = threadIdx.x;
     const Seg* __restrict__ S = ctx->segs;
@@ -989,10 +1001,11 @@ __global__ void __launch_bounds__(FIRST_THREADS)
                 const int j = tid + q * THREADS;
                 c[q] = j < E ? ld_stream(cit + j) : 0;
             }
+            const int sb = stage_at<ITEMS>(tid);
 #pragma unroll
             for (int q = 0; q < ITEMS; ++q) {
                 const int j = tid + q * THREADS;
-                if (j < E) s_col[j] = c[q];
+                if (j < E) s_col[sb + q * (THREADS + THREADS / ITEMS)] = c[q];
             }
         }
         __syncthreads();
@@ -1032,7 +1045,7 @@ __global__ void __launch_bounds__(FIRST_THREADS)
                     ++r;
                     rend = r < nfull ? s_rowend[r] : 0x7fffffff;
                 } else {
-                    const int32_t v = s_col[y];
+                    const int32_t v = s_col[stage_at<ITEMS>(y)];
                     if ((uint32_t)v < (uint64_t)n) acc = min(acc, v);
                     if (count) {
                         const int b = col_block(v, shift, nb);
@@ -1047,7 +1060,7 @@ __global__ void __launch_bounds__(FIRST_THREADS)
                             // has the same block
                             const int rs = r > 0 ? s_rowend[r - 1] : 0;
                             cstart = cb >= 0 || y == 0 || (r > 0 && y == rs) ||
-                                     col_block(s_col[y - 1], shift, nb) != b;
+                                     col_block(s_col[stage_at<ITEMS>(y - 1)], shift, nb) != b;
                             cb = b;
                             clen = 0;
                         }
@@ -1131,7 +1144,9 @@ __global__ void k_feed_tiles(const Ctx* __restrict__ ctx, FeedBounds fb, int64_t
     out[c] = lo;
 }
 
-__host__ __device__ constexpr int k2_first_smem() { return (3 * (FIRST_THREADS * FIRST_ITEMS) + 2) * (int)sizeof(int32_t); }
+__host__ __device__ constexpr int k2_first_smem() {
+    return (3 * (FIRST_THREADS * FIRST_ITEMS) + 2 + FIRST_THREADS) * (int)sizeof(int32_t);
+}
 
 // a1, sparse iteration (Section 4.2's SpMSpV): only vertices whose gf
 // changed in the last iteration can lower a neighbour's minimum, and gf never
