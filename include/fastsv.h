@@ -96,7 +96,7 @@ typedef struct {
                               grandparent vector.  A block lists only the rows that have entries in it
                               (compressed rows).  Its first iteration runs before the copy, on the
                               caller's CSR (it gathers nothing), and counts the copy's sizes; the call
-                              then synchronises once more, to size the copy's row lists (workspace:
+                              then synchronises once more, to size (or check) the copy's row lists (workspace:
                               4m bytes of entries, 8 bytes per (row, block) pair, 8nb bytes per 1024
                               entries of counts).  Rows need not be sorted (unsorted rows give longer
                               row lists and slower merges, never other labels) */
@@ -205,7 +205,11 @@ fastsv_status fastsv_cc(fastsv_t h, int64_t n, const void* row_ptr, const int32_
  * memory recommended.  Same sizes and layout as fastsv_cc.  For a
  * column-blocked graph (without validation) col_idx is copied in chunks on a
  * stream of the handle's own, and the first iteration works on every chunk
- * once it has landed; fastsv_get_stats' ms_total then includes the copy.
+ * once it has landed; when the handle's run arrays are large enough from an
+ * earlier call, every chunk is also copied into the column blocks at once
+ * (the call checks the copy's totals when all chunks are in, and copies
+ * again if the runs did not fit).  fastsv_get_stats' ms_total then includes
+ * the copy.
  */
 fastsv_status fastsv_cc_host(fastsv_t h, int64_t n, const void* row_ptr_host, const int32_t* col_idx_host,
                              int32_t* labels_host, void* stream);

@@ -567,12 +567,19 @@ static int choose_col_blocks(const fastsv_ctx* h, int64_t n, int64_t m) {
     return nb;
 }
 
-// counts (2 nb rows of tiles + 1), scan sums, the block copy's entries, and
-// the host-visible totals; the runs' arrays grow once their count is known
+// counts (2 nb rows of tiles + 1), scan sums, the block copy's entries, the
+// chunks' layouts and totals, and the host-visible checks; the runs' arrays
+// grow once their count is known
 static fastsv_status ensure_block_workspace(fastsv_ctx* h, int nb, int64_t tiles, int64_t m) {
     fastsv_status st;
     if (!h->d_build_scalars) {
-        if ((st = dev_alloc(h, (void**)&h->d_build_scalars, 4 * 2 * MAX_COL_BLOCKS)) != FASTSV_OK) return st;
+        if ((st = dev_alloc(h, (void**)&h->d_build_scalars, 8 * 4)) != FASTSV_OK) return st;
+    }
+    if (!h->d_clay) {
+        if ((st = dev_alloc(h, (void**)&h->d_clay, sizeof(ChunkLayout) * MAX_FEED_CHUNKS)) != FASTSV_OK) return st;
+    }
+    if (!h->d_ctot) {
+        if ((st = dev_alloc(h, (void**)&h->d_ctot, 4 * 2 * MAX_COL_BLOCKS * MAX_FEED_CHUNKS)) != FASTSV_OK) return st;
     }
     const int64_t T1 = tiles + 1;
     const int64_t cells = 2 * (int64_t)nb * T1;
@@ -598,13 +605,15 @@ static fastsv_status ensure_block_workspace(fastsv_ctx* h, int nb, int64_t tiles
     return FASTSV_OK;
 }
 
-static fastsv_status ensure_run_workspace(fastsv_ctx* h, int64_t runs, int nb) {
+// rowsB / endsB for `runs` runs and `slots` leading slots (one per (chunk,
+// block) pair)
+static fastsv_status ensure_run_workspace(fastsv_ctx* h, int64_t runs, int64_t slots) {
     fastsv_status st;
-    if (runs + nb + 1 > h->cap_runs) {
+    if (runs + slots > h->cap_runs) {
         dev_free((void**)&h->d_rowsB);
         dev_free((void**)&h->d_endsB);
         h->cap_runs = 0;
-        const int64_t c = runs + runs / 8 + nb + 1;  // room to grow a little between calls
+        const int64_t c = runs + runs / 8 + slots;  // room to grow a little between calls
         if ((st = dev_alloc(h, (void**)&h->d_rowsB, (size_t)c * 4)) != FASTSV_OK) return st;
         if ((st = dev_alloc(h, (void**)&h->d_endsB, (size_t)c * 4)) != FASTSV_OK) {
             dev_free((void**)&h->d_rowsB);
@@ -615,11 +624,6 @@ static fastsv_status ensure_run_workspace(fastsv_ctx* h, int64_t runs, int nb) {
     return FASTSV_OK;
 }
 
-// one iteration on segment 0's own tiles (BUILD_TILE items each), launched
-// kernel by kernel: the first iteration of a column-blocked solve.  Its SpMV
-// (k2_first) gathers nothing, so the per-tile merge-path search is most of
-// its work: 64 threads x 16 items spend one search on 16 items.  It also
-// counts every tile's entries and runs per column block for the block copy.
 // col_idx of a fastsv_cc_host call still in host memory: the first iteration
 // of a column-blocked solve reads it chunk by chunk as the copies land
 struct HostFeed {
@@ -639,18 +643,67 @@ static fastsv_status ensure_feed(fastsv_ctx* h) {
     return FASTSV_OK;
 }
 
-static fastsv_status first_iteration_unblocked(fastsv_ctx* h, int rp64, int nb, int shift, int64_t m,
-                                               const HostFeed* feed, cudaStream_t s) {
+// The column-block copy of one chunk of the first iteration's tiles (range:
+// the chunks' tile bounds on the device, or null for one chunk of every
+// tile): scan the chunk's counts, place its blocks, and (when the runs'
+// arrays are already there) split its entries into them.
+struct BlockBuild {
+    int nb, shift, chunks;
+    int64_t tiles, m;
+    const int64_t* range;
+};
+
+template <typename RP>
+static fastsv_status launch_chunk_split(fastsv_ctx* h, const BlockBuild& B, int c, cudaStream_t s) {
+    int per_sm = 0;
+    FSV_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k_block_split<RP>, SPLIT_THREADS, 0));
+    const int grid = (per_sm > 0 ? per_sm : 1) * h->num_sms;
+    k_block_split<RP><<<grid, SPLIT_THREADS, 0, s>>>(h->d_ctx, h->d_clay, c, B.nb, B.shift, B.tiles + 1, B.range,
+                                                    h->d_counts, h->d_colB, h->d_rowsB, h->d_endsB, B.m, h->cap_runs);
+    h->pending_fixed_launches += 1;
+    FSV_CUDA(h, cudaGetLastError());
+    return FASTSV_OK;
+}
+
+static fastsv_status launch_chunk_layout(fastsv_ctx* h, const BlockBuild& B, int c, cudaStream_t s) {
+    const int64_t T1 = B.tiles + 1;
+    const int rows = 2 * B.nb;
+    const int pieces = (int)((T1 + SCAN_CHUNK - 1) / SCAN_CHUNK);
+    int32_t* tot = h->d_ctot + (int64_t)c * rows;
+    k_scan_chunk_sums<<<(unsigned)(rows * pieces), SCAN_THREADS, 0, s>>>(h->d_counts, T1, pieces, h->d_sums, B.range, c);
+    k_scan_sums<<<rows, 1024, 0, s>>>(h->d_sums, pieces, tot);
+    k_scan_apply<<<(unsigned)(rows * pieces), SCAN_THREADS, 0, s>>>(h->d_counts, h->d_counts, T1, pieces, h->d_sums,
+                                                                  B.range, c);
+    k_chunk_layout<<<1, 32, 0, s>>>(h->d_ctx, tot, B.nb, B.range, c, h->d_clay);
+    h->pending_fixed_launches += 4;
+    FSV_CUDA(h, cudaGetLastError());
+    return FASTSV_OK;
+}
+
+// one iteration on segment 0's own tiles (BUILD_TILE items each), launched
+// kernel by kernel: the first iteration of a column-blocked solve.  Its SpMV
+// (k2_first) gathers nothing, so the per-tile merge-path search is most of
+// its work: 64 threads x 16 items spend one search on 16 items.  It also
+// counts every tile's entries and runs per column block for the block copy.
+// Fed from host memory (feed), col_idx arrives in FEED_CHUNKS pieces and
+// every piece's tiles run once it has landed; with `pipelined`, every
+// chunk's block copy follows right behind (its runs' arrays are sized from
+// an earlier call of the handle and checked afterwards).
+template <typename RP>
+static fastsv_status first_iteration_unblocked(fastsv_ctx* h, const BlockBuild& B, const HostFeed* feed,
+                                               bool pipelined, cudaStream_t s) {
+    const int rp64 = sizeof(RP) == 8;
     IterKernels K;
     fastsv_status st = iter_kernels(h, rp64, rp64, 8, &K);
     if (st != FASTSV_OK) return st;
-    const void* spmv = rp64 ? (const void*)k2_first<int64_t> : (const void*)k2_first<int32_t>;
+    const void* spmv = (const void*)k2_first<RP>;
     const int smem = k2_first_smem();
     int per_sm = 0;
     FSV_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, spmv, FIRST_THREADS, smem));
     const int grid = (per_sm > 0 ? per_sm : 1) * h->num_sms;
     Ctx* ctx = h->d_ctx;
     int32_t* cnt = h->d_counts;
+    int nb = B.nb, shift = B.shift;
     cudaGraphConditionalHandle none = 0;
     int no_cond = 0;
     void* a_begin[] = {(void*)&ctx, (void*)&none, (void*)&no_cond};
@@ -672,7 +725,7 @@ static fastsv_status first_iteration_unblocked(fastsv_ctx* h, int rp64, int nb, 
         FeedBounds fb;
         memset(&fb, 0, sizeof(fb));
         fb.chunks = FEED_CHUNKS;
-        for (int c = 0; c <= FEED_CHUNKS; ++c) fb.b[c] = m * c / FEED_CHUNKS;
+        for (int c = 0; c <= FEED_CHUNKS; ++c) fb.b[c] = B.m * c / FEED_CHUNKS;
         k_feed_tiles<<<1, 32, 0, s>>>(ctx, fb, h->d_feed_tiles);
         FSV_CUDA(h, cudaEventRecord(h->feed_ev[0], s));
         FSV_CUDA(h, cudaStreamWaitEvent(h->feed_stream, h->feed_ev[0], 0));
@@ -689,6 +742,10 @@ static fastsv_status first_iteration_unblocked(fastsv_ctx* h, int rp64, int nb, 
             int chunk = c;
             void* a_spmv[] = {(void*)&ctx, (void*)&cnt, (void*)&nb, (void*)&shift, (void*)&range, (void*)&chunk};
             FSV_CUDA(h, cudaLaunchKernel(spmv, dim3(grid), dim3(FIRST_THREADS), a_spmv, smem, s));
+            if (pipelined) {
+                if ((st = launch_chunk_layout(h, B, c, s)) != FASTSV_OK) return st;
+                if ((st = launch_chunk_split<RP>(h, B, c, s)) != FASTSV_OK) return st;
+            }
         }
         h->pending_fixed_launches += 1 + FEED_CHUNKS;
     }
@@ -698,49 +755,42 @@ static fastsv_status first_iteration_unblocked(fastsv_ctx* h, int rp64, int nb, 
     return FASTSV_OK;
 }
 
-// The block copy after the first iteration counted it: scan the counts over
-// the tiles, read the blocks' totals (one synchronisation: the runs' arrays
-// are sized by them), split the entries into the blocks, and describe the
-// blocks as segments 1..nb with their own merge-path tiles.
+// The block copy after the first iteration counted it.  Unless the chunks
+// were already copied (pipelined): scan the counts over all tiles (one
+// chunk), place the blocks, and split the entries.  Either way the host
+// reads the copy's totals (one synchronisation: the runs' arrays are sized,
+// or checked, by them), and the blocks become segments 1 .. nb C with their
+// own merge-path tiles.
 template <typename RP>
-static fastsv_status build_blocks(fastsv_ctx* h, int nb, int shift, int64_t tiles, int64_t m, int32_t tile,
-                                  cudaStream_t s) {
-    const int64_t T1 = tiles + 1;
-    const int64_t chunks = (T1 + SCAN_CHUNK - 1) / SCAN_CHUNK;
-    const int segs = 2 * nb;
-    const int ch = (int)chunks;
-    k_scan_chunk_sums<<<(unsigned)(segs * chunks), SCAN_THREADS, 0, s>>>(h->d_counts, T1, ch, h->d_sums);
-    k_scan_sums<<<segs, 1024, 0, s>>>(h->d_sums, ch);
-    k_scan_apply<<<(unsigned)(segs * chunks), SCAN_THREADS, 0, s>>>(h->d_counts, h->d_counts, T1, ch, h->d_sums);
-    k_block_totals<<<1, 64, 0, s>>>(h->d_counts, nb, T1, h->d_build_scalars);
-    h->pending_fixed_launches += 4;
-    FSV_CUDA(h, cudaGetLastError());
-    FSV_CUDA(h, cudaMemcpyAsync(h->h_scalar, h->d_build_scalars, (size_t)segs * 4, cudaMemcpyDeviceToHost, s));
-    FSV_CUDA(h, cudaStreamSynchronize(s));
-    BlockLayout L;
-    memset(&L, 0, sizeof(L));
-    L.nb = nb;
-    L.shift = shift;
-    L.T1 = T1;
-    const int32_t* tot = (const int32_t*)h->h_scalar;
-    for (int b = 0; b < nb; ++b) {
-        L.ebase[b + 1] = L.ebase[b] + (uint32_t)tot[b];
-        L.pbase[b + 1] = L.pbase[b] + (uint32_t)tot[nb + b];
+static fastsv_status build_blocks(fastsv_ctx* h, const BlockBuild& B, bool pipelined, int32_t tile, cudaStream_t s) {
+    fastsv_status st;
+    const int C = pipelined ? B.chunks : 1;
+    BlockBuild one = B;
+    if (!pipelined) {
+        one.chunks = 1;
+        one.range = nullptr;
+        if ((st = launch_chunk_layout(h, one, 0, s)) != FASTSV_OK) return st;
     }
-    if (L.ebase[nb] != m) return FASTSV_ERR_INVALID_GRAPH;  // row_ptr not a valid CSR of m entries
-    const int64_t runs = L.pbase[nb];
-    fastsv_status st = ensure_run_workspace(h, runs, nb);
-    if (st != FASTSV_OK) return st;
+    k_chunk_check<<<1, 32, 0, s>>>(h->d_clay, C, B.nb, h->d_build_scalars);
+    h->pending_fixed_launches += 1;
+    FSV_CUDA(h, cudaGetLastError());
+    FSV_CUDA(h, cudaMemcpyAsync(h->h_scalar, h->d_build_scalars, 3 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    FSV_CUDA(h, cudaStreamSynchronize(s));
+    const int64_t ends = h->h_scalar[0], runs = h->h_scalar[1], contiguous = h->h_scalar[2];
+    if (ends != B.m || !contiguous) return FASTSV_ERR_INVALID_GRAPH;  // row_ptr not a valid CSR of m entries
+    const int64_t slots = (int64_t)B.nb * C;
+    const bool fits = pipelined && runs + slots <= h->cap_runs;
+    if ((st = ensure_run_workspace(h, runs, slots)) != FASTSV_OK) return st;
     h->last_runs = runs;
-    Ctx* ctx = h->d_ctx;
-    int per_sm = 0;
-    FSV_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k_block_split<RP>, SPLIT_THREADS, 0));
-    const int grid = (per_sm > 0 ? per_sm : 1) * h->num_sms;
-    k_block_split<RP><<<grid, SPLIT_THREADS, 0, s>>>(ctx, L, h->d_counts, h->d_colB, h->d_rowsB, h->d_endsB, m, runs);
-    k_setup_blocks<<<1, 1, 0, s>>>(ctx, L, h->d_colB, h->d_rowsB, h->d_endsB, tile);
-    k_scan_tiles<<<1, 1024, 0, s>>>(ctx);
-    k_partition<int32_t><<<setup_grid(h), 256, 0, s>>>(ctx);
-    h->pending_fixed_launches += 4;
+    if (!fits) {
+        // split now (one chunk), or again with room for every run
+        for (int c = 0; c < C; ++c)
+            if ((st = launch_chunk_split<RP>(h, pipelined ? B : one, c, s)) != FASTSV_OK) return st;
+    }
+    k_setup_blocks<<<1, 256, 0, s>>>(h->d_ctx, h->d_clay, C, B.nb, h->d_colB, h->d_rowsB, h->d_endsB, tile);
+    k_scan_tiles<<<1, 1024, 0, s>>>(h->d_ctx);
+    k_partition<int32_t><<<setup_grid(h), 256, 0, s>>>(h->d_ctx);
+    h->pending_fixed_launches += 3;
     FSV_CUDA(h, cudaGetLastError());
     return FASTSV_OK;
 }
@@ -763,11 +813,13 @@ static fastsv_status solve_single(fastsv_ctx* h, int64_t n, int64_t m, const voi
     // the block copy first (BUILD_TILE items per tile)
     const int64_t tile0 = nb_eff > 1 ? (int64_t)BUILD_TILE : tile;
     const int64_t t2 = m > 0 ? (n + m + tile0 - 1) / tile0 : 0;
-    // the blocks' tiles: every run holds at least one entry, so runs <= m
-    const int64_t t2b = nb_eff > 1 ? (2 * m) / tile + 2 * (nb_eff + 1) : 0;
+    // the blocks' tiles: every run holds at least one entry, so runs <= m;
+    // one segment per block and chunk of the copy
+    const int64_t bsegs = nb_eff > 1 ? (int64_t)nb_eff * FEED_CHUNKS : 0;
+    const int64_t t2b = nb_eff > 1 ? (2 * m) / tile + 2 * (bsegs + 1) : 0;
     const int64_t t3 = (n + K3_TILE - 1) / K3_TILE;
     if (t2 > INT32_MAX || t2b > INT32_MAX || t3 > INT32_MAX) return FASTSV_ERR_UNSUPPORTED;
-    fastsv_status st = ensure_workspace(h, n, t2 > t2b ? t2 : t2b, t3, 1 + nb_eff);
+    fastsv_status st = ensure_workspace(h, n, t2 > t2b ? t2 : t2b, t3, 1 + bsegs);
     if (st != FASTSV_OK) return st;
     if (nb_eff > 1 && (st = ensure_block_workspace(h, nb_eff, t2, m)) != FASTSV_OK) return st;
     // col_idx still in host memory: a blocked solve without validation copies
@@ -810,14 +862,21 @@ static fastsv_status solve_single(fastsv_ctx* h, int64_t n, int64_t m, const voi
         // The graph's first iteration needs no gathers (gf is still the
         // identity), so it gains nothing from column blocks: it runs on the
         // original CSR, over the build's tiles (BUILD_TILE items), before the
-        // block copy.
+        // block copy.  Fed from host memory, and with runs' arrays from an
+        // earlier call, every chunk is copied into the blocks as soon as its
+        // entries are in (checked, and redone if the runs did not fit).
         k_init_state<<<setup_grid(h), 256, 0, s>>>(h->d_ctx);
         h->pending_fixed_launches += 1;
-        if ((st = first_iteration_unblocked(h, rp64, nb_eff, shift, m, fed ? &feed : nullptr, s)) != FASTSV_OK)
-            return st;
+        const bool pipelined = fed && h->cap_runs > 0;
+        BlockBuild B{nb_eff, shift, FEED_CHUNKS, t2, m, fed ? h->d_feed_tiles : nullptr};
+        if (fed && (st = ensure_feed(h)) != FASTSV_OK) return st;
+        B.range = fed ? h->d_feed_tiles : nullptr;
+        st = rp64 ? first_iteration_unblocked<int64_t>(h, B, fed ? &feed : nullptr, pipelined, s)
+                  : first_iteration_unblocked<int32_t>(h, B, fed ? &feed : nullptr, pipelined, s);
+        if (st != FASTSV_OK) return st;
         // split the entries into column blocks of compressed rows
-        st = rp64 ? build_blocks<int64_t>(h, nb_eff, shift, t2, m, (int32_t)tile, s)
-                  : build_blocks<int32_t>(h, nb_eff, shift, t2, m, (int32_t)tile, s);
+        st = rp64 ? build_blocks<int64_t>(h, B, pipelined, (int32_t)tile, s)
+                  : build_blocks<int32_t>(h, B, pipelined, (int32_t)tile, s);
         if (st != FASTSV_OK) return st;
         loop_rp64 = 0;
     } else {
@@ -956,6 +1015,8 @@ fastsv_status fastsv_destroy(fastsv_t h) {
     dev_free((void**)&h->d_rowsB);
     dev_free((void**)&h->d_endsB);
     dev_free((void**)&h->d_build_scalars);
+    dev_free((void**)&h->d_clay);
+    dev_free((void**)&h->d_ctot);
     dev_free((void**)&h->d_feed_tiles);
     if (h->feed_stream) cudaStreamDestroy(h->feed_stream);
     for (cudaEvent_t& ev : h->feed_ev)

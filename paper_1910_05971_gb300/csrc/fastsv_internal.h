@@ -68,16 +68,18 @@ struct fastsv_ctx {
     int64_t cap_n = 0;
 
     // column-blocked copy of a large graph (see k_block_split)
-    int32_t* d_counts = nullptr;    // per (block, tile) entries and runs, scanned in place
+    int32_t* d_counts = nullptr;    // per (block, tile) entries and runs, scanned in place per chunk
     int64_t cap_blk = 0;
     int32_t* d_sums = nullptr;
     int64_t cap_sums = 0;
-    int32_t* d_colB = nullptr;      // the entries, block after block
+    int32_t* d_colB = nullptr;      // the entries, chunk after chunk, in a chunk block after block
     int64_t cap_colB = 0;
     int32_t* d_rowsB = nullptr;     // graph row of every run
-    int32_t* d_endsB = nullptr;     // end of every run inside its block (one leading 0 per block)
+    int32_t* d_endsB = nullptr;     // end of every run inside its (chunk, block) (one leading 0 each)
     int64_t cap_runs = 0;
-    int32_t* d_build_scalars = nullptr;  // blocks' totals for the host
+    fsv::ChunkLayout* d_clay = nullptr;  // per chunk: where its blocks start
+    int32_t* d_ctot = nullptr;           // per chunk: entries and runs of each block
+    int64_t* d_build_scalars = nullptr;  // the copy's totals and consistency for the host
     int64_t last_runs = 0;
     int last_col_blocks = 1;
 

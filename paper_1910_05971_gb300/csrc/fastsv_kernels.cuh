@@ -178,6 +178,7 @@ __global__ void k_setup_single(Ctx* ctx, SingleParams prm, WsPtrs ws) {
     ctx->frontier_overflow = 0;
     ctx->sparse_div = prm.sparse_div;
     ctx->sparse_iters = 0;
+    ctx->blk_chunks = 1;
     for (int i = 0; i < TRACE_LEN; ++i) ctx->sum.trace[i] = 0;
 }
 
@@ -250,6 +251,7 @@ __global__ void k_setup_batched(Ctx* ctx, BatchParams prm, WsPtrs ws) {
         ctx->frontier_overflow = 0;
         ctx->sparse_div = prm.sparse_div;
         ctx->sparse_iters = 0;
+        ctx->blk_chunks = 1;
         for (int i = 0; i < TRACE_LEN; ++i) ctx->sum.trace[i] = 0;
     }
 }
@@ -397,27 +399,32 @@ __global__ void k_validate(Ctx* ctx, int check_sym) {
 //
 // Layout of the block copy (compressed rows: a block lists only the rows that
 // have entries in it).  The copy is cut along the merge-path tiles of the
-// graph's own CSR (the first iteration's tiles, BUILD_TILE items each).
-// Inside a tile, a "run" is a maximal sequence of consecutive entries of one
-// row whose columns fall in one block; when rows are sorted by column a row
-// has exactly one run per block it touches.  Block b holds, tile after tile,
-// the tile's runs of block b in tile order (a stable partition of the tile's
-// entries by block):
-//   colB[ebase_b + ...]          the entries (global column ids)
-//   rowsB[pbase_b + i]           global row of run i; bit 31 set when the
-//                                row may have another run in block b (the
-//                                row crosses a tile boundary, or the tile's
-//                                rows are not sorted by block), so its
-//                                partial minimum must merge atomically
-//   endsB[pbase_b + b + i + 1]   end of run i inside block b's entries
-//                                (endsB[pbase_b + b] = 0): block b is a CSR
-//                                over its runs, walked by the same merge-path
-//                                SpMV as the graph itself.
+// graph's own CSR (the first iteration's tiles, BUILD_TILE items each), and
+// the tiles are grouped into C chunks of consecutive tiles (C = 1, or one
+// chunk per piece in which col_idx arrives from host memory, so that a chunk
+// is copied as soon as its entries are there).  Inside a tile, a "run" is a
+// maximal sequence of consecutive entries of one row whose columns fall in
+// one block; when rows are sorted by column a row has exactly one run per
+// block it touches.  Chunk c occupies the entries [Y_c, Y_{c+1}) of colB
+// (the same entries as in the CSR), block after block; block b of chunk c
+// holds, tile after tile, the tile's runs of block b in tile order (a stable
+// partition of the tile's entries by block):
+//   colB[ebase_cb + ...]          the entries (global column ids)
+//   rowsB[pbase_cb + i]           global row of run i; bit 31 set when the
+//                                 row may have another run in the block (the
+//                                 row crosses a tile boundary, or the tile's
+//                                 rows are not sorted by block), so its
+//                                 partial minimum must merge atomically
+//   endsB[pbase_cb + s + i + 1]   end of run i inside the block's entries of
+//                                 the chunk, s = c nb + b (endsB[pbase_cb +
+//                                 s] = 0): every (chunk, block) is a CSR over
+//                                 its runs, walked by the same merge-path
+//                                 SpMV as the graph itself.
 // The first iteration's SpMV counts every tile's entries and runs per block;
-// an exclusive scan over tiles gives every (tile, block) its offsets.
+// an exclusive scan over a chunk's tiles gives every (tile, block) its
+// offsets, and the chunk's totals place its blocks (ChunkLayout).
 // ---------------------------------------------------------------------------
 
-constexpr int MAX_COL_BLOCKS = 32;
 constexpr int32_t ROW_SHARED = (int32_t)0x80000000u;  // rowsB flag: merge this run's minimum atomically
 
 __device__ __forceinline__ int col_block(int32_t c, int shift, int nb) {
@@ -428,15 +435,6 @@ __device__ __forceinline__ int col_block(int32_t c, int shift, int nb) {
 constexpr int BUILD_THREADS = 128;  // CTA size and items per thread of the block-split kernel
 constexpr int BUILD_ITEMS = 8;
 constexpr int BUILD_TILE = BUILD_THREADS * BUILD_ITEMS;
-
-// offsets of the blocks' entries and runs in colB / rowsB (host-computed
-// from the scanned counts; entry b + 1 is the end of block b)
-struct BlockLayout {
-    int32_t nb, shift;
-    int64_t T1;  // stride of one block's count row: tiles + 1
-    int64_t ebase[MAX_COL_BLOCKS + 1];
-    int64_t pbase[MAX_COL_BLOCKS + 1];
-};
 
 // The block copy: for every tile of segment 0 (the tiles the first
 // iteration counted), a stable partition of its entries by column block.
@@ -454,9 +452,13 @@ constexpr int SPLIT_THREADS = 32 * SPLIT_WARPS;
 constexpr int SPLIT_BATCH = 8;                  // rounds whose column ids are loaded together
 constexpr int SPLIT_RUNS = 32 * SPLIT_BATCH;    // runs a batch can start
 
+// This launch copies chunk `chunk` (tiles [range[chunk], range[chunk + 1]),
+// or every tile when range is null); p_total is the length of rowsB and
+// endsB: no write goes at or beyond it (the host checks that the runs fit).
 template <typename RP>
 __global__ void __launch_bounds__(32 * SPLIT_WARPS)
-    k_block_split(const Ctx* __restrict__ ctx, BlockLayout L, const int32_t* __restrict__ cnt,
+    k_block_split(const Ctx* __restrict__ ctx, const ChunkLayout* __restrict__ lay, int chunk, int nb, int shift,
+                  int64_t T1, const int64_t* __restrict__ range, const int32_t* __restrict__ cnt,
                   int32_t* __restrict__ colB, int32_t* __restrict__ rowsB, int32_t* __restrict__ endsB,
                   int64_t m_total, int64_t p_total) {
     __shared__ int16_t s_rowof[SPLIT_WARPS][BUILD_TILE];    // row starting at a position (valid where s_rs is set)
@@ -469,16 +471,18 @@ __global__ void __launch_bounds__(32 * SPLIT_WARPS)
     __shared__ int8_t s_rb[SPLIT_WARPS][SPLIT_RUNS];         //   block
     __shared__ long long s_eb[MAX_COL_BLOCKS], s_pb[MAX_COL_BLOCKS];
     const Seg S0 = ctx->segs[0];
-    const int nb = L.nb, shift = L.shift;
+    const ChunkLayout& L = lay[chunk];
+    const int sub0 = chunk * nb;  // run CSRs of earlier (chunk, block) pairs: one leading slot each
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     if ((int)threadIdx.x < nb) {
         s_eb[threadIdx.x] = L.ebase[threadIdx.x];
-        s_pb[threadIdx.x] = L.pbase[threadIdx.x];
+        s_pb[threadIdx.x] = L.pbase[threadIdx.x] + sub0;  // + b: endsB index of run 0; - sub0: rowsB index
         if (blockIdx.x == 0) {  // the end of the block's last run
             const int b = threadIdx.x;
             const int64_t pb = L.pbase[b + 1] - L.pbase[b];
-            if (L.pbase[b] + b + pb <= p_total + nb) endsB[L.pbase[b] + b + pb] = (int32_t)(L.ebase[b + 1] - L.ebase[b]);
+            const int64_t at = L.pbase[b] + sub0 + b + pb;
+            if (at < p_total) endsB[at] = (int32_t)(L.ebase[b + 1] - L.ebase[b]);
         }
     }
     __syncthreads();
@@ -488,7 +492,9 @@ __global__ void __launch_bounds__(32 * SPLIT_WARPS)
     const int32_t* __restrict__ tile_row = ctx->k2_tile_row + S0.k2_tile0;
     unsigned* rsw = s_rs[w];
     int16_t* rowof = s_rowof[w];
-    for (int64_t t = (int64_t)blockIdx.x * SPLIT_WARPS + w; t < T; t += (int64_t)gridDim.x * SPLIT_WARPS) {
+    const int64_t t_end = range ? min(range[chunk + 1], T) : T;
+    for (int64_t t = (range ? range[chunk] : 0) + (int64_t)blockIdx.x * SPLIT_WARPS + w; t < t_end;
+         t += (int64_t)gridDim.x * SPLIT_WARPS) {
         const int64_t d0 = t * BUILD_TILE, d1 = min(d0 + BUILD_TILE, n + m);
         const int64_t x0 = tile_row[t];
         const int64_t x1 = t + 1 < T ? (int64_t)tile_row[t + 1] : n;
@@ -501,8 +507,8 @@ __global__ void __launch_bounds__(32 * SPLIT_WARPS)
         if (E <= 0) continue;
         rsw[lane] = 0u;
         if (lane < nb) {
-            s_pos[w][lane] = cnt[(int64_t)lane * L.T1 + t];
-            s_run[w][lane] = cnt[(int64_t)(nb + lane) * L.T1 + t];
+            s_pos[w][lane] = cnt[(int64_t)lane * T1 + t];
+            s_run[w][lane] = cnt[(int64_t)(nb + lane) * T1 + t];
         }
         const bool first_whole = rp_at(rp, x0) >= y0;  // row x0 starts inside the tile
         __syncwarp();
@@ -574,8 +580,8 @@ __global__ void __launch_bounds__(32 * SPLIT_WARPS)
                 const int row = bits ? rowof[wd * 32 + 31 - __clz(bits)] : 0;
                 const bool shared = (row == 0 && !first_whole) || row >= nfull;
                 const int64_t pi = s_pb[b] + s_ri[w][k2];
-                if (pi < p_total) {
-                    rowsB[pi] = (int32_t)(x0 + row) | (shared ? ROW_SHARED : 0);
+                if (pi + b < p_total) {
+                    rowsB[pi - sub0] = (int32_t)(x0 + row) | (shared ? ROW_SHARED : 0);
                     endsB[pi + b] = s_rp[w][k2];  // the block's previous run ends where this one starts
                 }
             }
@@ -585,23 +591,20 @@ __global__ void __launch_bounds__(32 * SPLIT_WARPS)
         // tile, so every run of this tile merges atomically
         if (__any_sync(0xffffffffu, desc)) {
             for (int b = 0; b < nb; ++b) {
-                const int r0 = cnt[(int64_t)(nb + b) * L.T1 + t], r1 = s_run[w][b];
+                const int r0 = cnt[(int64_t)(nb + b) * T1 + t], r1 = s_run[w][b];
                 for (int i = r0 + lane; i < r1; i += 32)
-                    if (s_pb[b] + i < p_total) rowsB[s_pb[b] + i] |= ROW_SHARED;
+                    if (s_pb[b] + i < p_total) rowsB[s_pb[b] - sub0 + i] |= ROW_SHARED;
             }
         }
         __syncwarp();
     }
 }
 
-// the scanned totals of every block (entries, then runs) for the host
-__global__ void k_block_totals(const int32_t* cnt, int nb, int64_t T1, int32_t* out) {
-    const int i = threadIdx.x;
-    if (i < 2 * nb) out[i] = cnt[(int64_t)i * T1 + (T1 - 1)];
-}
-
-// exclusive scan of nb segments of L = n+1 int32 each (block-major), in
-// chunks of SCAN_CHUNK: chunk sums, per-segment scan of the sums, apply
+// exclusive scan of rows of int32 (row r at in + r L), over the tiles of
+// one chunk (columns [range[rc], range[rc + 1]) of every row, or [0, L) when
+// range is null), in pieces of SCAN_CHUNK: piece sums, per-row scan of the
+// sums (whose total is the chunk's), apply.  Launched with `pieces` CTAs per
+// row, enough for any chunk; CTAs past the chunk's end do nothing.
 constexpr int SCAN_THREADS = 256;
 constexpr int SCAN_ITEMS = 16;
 constexpr int SCAN_CHUNK = SCAN_THREADS * SCAN_ITEMS;
@@ -632,72 +635,124 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* s_warp, int* tot
     return before;
 }
 
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan_chunk_sums(const int32_t* in, int64_t L, int chunks,
-                                                                 int32_t* sums) {
+__device__ __forceinline__ void scan_bounds(const int64_t* range, int rc, int64_t L, int64_t& t0, int64_t& t1) {
+    t0 = range ? range[rc] : 0;
+    t1 = range ? range[rc + 1] : L;
+    t1 = t1 < L ? t1 : L;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_chunk_sums(const int32_t* in, int64_t L, int pieces,
+                                                                 int32_t* sums, const int64_t* range, int rc) {
     __shared__ int s_warp[32];
-    const int seg = blockIdx.x / chunks, c = blockIdx.x % chunks;
-    const int32_t* p = in + (int64_t)seg * L;
-    const int64_t base = (int64_t)c * SCAN_CHUNK;
+    const int row = blockIdx.x / pieces, c = blockIdx.x % pieces;
+    int64_t t0, t1;
+    scan_bounds(range, rc, L, t0, t1);
+    const int32_t* p = in + (int64_t)row * L;
+    const int64_t base = t0 + (int64_t)c * SCAN_CHUNK;
     int acc = 0;
-    for (int i = threadIdx.x; i < SCAN_CHUNK; i += SCAN_THREADS) {
-        int64_t j = base + i;
-        if (j < L) acc += p[j];
-    }
+    if (base < t1)
+        for (int i = threadIdx.x; i < SCAN_CHUNK; i += SCAN_THREADS) {
+            int64_t j = base + i;
+            if (j < t1) acc += p[j];
+        }
     int total = 0;
     block_exclusive_scan(acc, s_warp, &total);
     if (threadIdx.x == 0) sums[blockIdx.x] = total;
 }
 
-__global__ void __launch_bounds__(1024) k_scan_sums(int32_t* sums, int chunks) {
+// one CTA per row; totals[row]: the row's sum over the chunk
+__global__ void __launch_bounds__(1024) k_scan_sums(int32_t* sums, int pieces, int32_t* totals) {
     __shared__ int s_warp[32];
-    int32_t* p = sums + (int64_t)blockIdx.x * chunks;  // one CTA per segment
+    int32_t* p = sums + (int64_t)blockIdx.x * pieces;
     int carry = 0;
-    for (int base = 0; base < chunks; base += 1024) {
+    for (int base = 0; base < pieces; base += 1024) {
         int i = base + threadIdx.x;
-        int v = i < chunks ? p[i] : 0;
+        int v = i < pieces ? p[i] : 0;
         int total = 0;
         int ex = block_exclusive_scan(v, s_warp, &total);
-        if (i < chunks) p[i] = carry + ex;
+        if (i < pieces) p[i] = carry + ex;
         carry += total;
     }
+    if (threadIdx.x == 0) totals[blockIdx.x] = carry;
 }
 
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan_apply(const int32_t* in, int32_t* out, int64_t L, int chunks,
-                                                            const int32_t* sums) {
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_apply(const int32_t* in, int32_t* out, int64_t L, int pieces,
+                                                            const int32_t* sums, const int64_t* range, int rc) {
     __shared__ int s_warp[32];
-    const int seg = blockIdx.x / chunks, c = blockIdx.x % chunks;
-    const int32_t* p = in + (int64_t)seg * L;
-    int32_t* q = out + (int64_t)seg * L;
-    const int64_t base = (int64_t)c * SCAN_CHUNK + (int64_t)threadIdx.x * SCAN_ITEMS;
+    const int row = blockIdx.x / pieces, c = blockIdx.x % pieces;
+    int64_t t0, t1;
+    scan_bounds(range, rc, L, t0, t1);
+    if (t0 + (int64_t)c * SCAN_CHUNK >= t1) return;  // CTA-uniform: past the chunk's end
+    const int32_t* p = in + (int64_t)row * L;
+    int32_t* q = out + (int64_t)row * L;
+    const int64_t base = t0 + (int64_t)c * SCAN_CHUNK + (int64_t)threadIdx.x * SCAN_ITEMS;
     int v[SCAN_ITEMS];
     int acc = 0;
 #pragma unroll
     for (int k = 0; k < SCAN_ITEMS; ++k) {
         int64_t j = base + k;
-        v[k] = j < L ? p[j] : 0;
+        v[k] = j < t1 ? p[j] : 0;
         acc += v[k];
     }
     int run = sums[blockIdx.x] + block_exclusive_scan(acc, s_warp, nullptr);
 #pragma unroll
     for (int k = 0; k < SCAN_ITEMS; ++k) {
         int64_t j = base + k;
-        if (j < L) q[j] = run;
+        if (j < t1) q[j] = run;
         run += v[k];
     }
 }
 
-// segments 1..nb: the column blocks of graph 0 (compressed rows: block b's
-// runs are its rows, rowsB maps them to the graph's rows), which keeps only
-// its grandparent tiles
-__global__ void k_setup_blocks(Ctx* ctx, BlockLayout L, const int32_t* colB, const int32_t* rowsB,
-                               const int32_t* endsB, int32_t k2_tile) {
+// chunk `chunk`'s blocks from its scanned totals (tot: entries per block,
+// then runs per block): its entries start where its first tile's do, its
+// runs where the previous chunk's end
+__global__ void k_chunk_layout(const Ctx* __restrict__ ctx, const int32_t* __restrict__ tot, int nb,
+                               const int64_t* __restrict__ range, int chunk, ChunkLayout* lay) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const Seg& S = ctx->segs[0];
+    const int64_t T = S.k2_ntiles;
+    const int64_t t0 = range ? range[chunk] : 0;
+    int64_t e = t0 < T ? t0 * ctx->k2_tile - ctx->k2_tile_row[S.k2_tile0 + t0] : S.m;
+    int64_t p = chunk > 0 ? lay[chunk - 1].pbase[nb] : 0;
+    ChunkLayout& L = lay[chunk];
+    for (int b = 0; b < nb; ++b) {
+        L.ebase[b] = e;
+        L.pbase[b] = p;
+        e += (uint32_t)tot[b];
+        p += (uint32_t)tot[nb + b];
+    }
+    L.ebase[nb] = e;
+    L.pbase[nb] = p;
+}
+
+// for the host: out[0] the end of the last chunk's entries (m for a valid
+// CSR), out[1] the runs of all chunks, out[2] 1 when every chunk's entries
+// end where the next chunk's begin
+__global__ void k_chunk_check(const ChunkLayout* __restrict__ lay, int chunks, int nb, int64_t* out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int64_t ok = 1;
+    for (int c = 0; c + 1 < chunks; ++c) ok &= lay[c].ebase[nb] == lay[c + 1].ebase[0];
+    out[0] = lay[chunks - 1].ebase[nb];
+    out[1] = lay[chunks - 1].pbase[nb];
+    out[2] = ok;
+}
+
+// segments 1 .. nb C: the column blocks of graph 0, chunk by chunk (block b
+// of chunk c is segment 1 + b C + c, so a block's segments are adjacent;
+// compressed rows: the runs are the rows, rowsB maps them to the graph's
+// rows); graph 0 keeps only its grandparent tiles
+__global__ void __launch_bounds__(256) k_setup_blocks(Ctx* ctx, const ChunkLayout* __restrict__ lay, int chunks, int nb,
+                                                      const int32_t* colB, const int32_t* rowsB, const int32_t* endsB,
+                                                      int32_t k2_tile) {
     Seg* segs = ctx->segs;
     const Seg g = segs[0];
-    for (int b = 0; b < L.nb; ++b) {
+    for (int i = threadIdx.x; i < nb * chunks; i += blockDim.x) {
+        const int c = i / nb, b = i % nb;
+        const ChunkLayout& L = lay[c];
         const int64_t pb = L.pbase[b + 1] - L.pbase[b];
         const int64_t mb = L.ebase[b + 1] - L.ebase[b];
         Seg s = g;
-        s.rp = endsB + L.pbase[b] + b;
+        s.rp = endsB + L.pbase[b] + i;  // one leading slot per earlier (chunk, block) pair
         s.ci = colB + L.ebase[b];
         s.rowmap = rowsB + L.pbase[b];
         s.n = pb;
@@ -707,12 +762,16 @@ __global__ void k_setup_blocks(Ctx* ctx, BlockLayout L, const int32_t* colB, con
         s.active = 1;
         s.leader = 0;
         s.user = b;
-        segs[1 + b] = s;
+        segs[1 + b * chunks + c] = s;
     }
-    segs[0].k2_ntiles = 0;
-    ctx->num_segs = L.nb + 1;
-    ctx->k2_tile = k2_tile;
-    ctx->loop_iter = 0;  // an iteration run before the blocks is not the device loop's
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        segs[0].k2_ntiles = 0;
+        ctx->num_segs = 1 + nb * chunks;
+        ctx->blk_chunks = chunks;
+        ctx->k2_tile = k2_tile;
+        ctx->loop_iter = 0;  // an iteration run before the blocks is not the device loop's
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -763,19 +822,24 @@ __global__ void __launch_bounds__(THREADS, 1536 / THREADS) k2_spmv(Ctx* __restri
     const Seg* __restrict__ segs = ctx->segs;
     const int64_t total = ctx->k2_total;
     int64_t t_begin = 0, T = total;
+    const int chunks = ctx->blk_chunks;  // segments of one column block
     if (block >= 0) {
-        if (block + 1 >= ctx->num_segs) return;
-        t_begin = segs[1 + block].k2_tile0;
-        T = t_begin + segs[1 + block].k2_ntiles;
+        if (1 + (block + 1) * chunks > ctx->num_segs) return;
+        const Seg& first = segs[1 + block * chunks];
+        const Seg& last = segs[(block + 1) * chunks];
+        t_begin = first.k2_tile0;
+        T = last.k2_tile0 + last.k2_ntiles;
     }
     const bool merge = block >= 0;
-    // one segment for the whole launch (a column block, or a single graph):
-    // its state is checked once and no tile looks its segment up
-    const bool one_seg = block >= 0 || ctx->num_segs == 1;
-    const int32_t seg0 = block >= 0 ? 1 + block : 0;
+    // one graph for the whole launch (a column block, or a single graph):
+    // its state is checked once; with one segment (a block copied as one
+    // chunk, or a single graph) no tile looks its segment up either
+    const bool one_state = block >= 0 || ctx->num_segs == 1;
+    const bool one_seg = (block >= 0 && chunks == 1) || ctx->num_segs == 1;
+    const int32_t seg0 = block >= 0 ? 1 + block * chunks : 0;
     bool ident1 = false;
     int64_t ncol1 = 0;
-    if (one_seg) {
+    if (one_state) {
         const Seg& L = segs[segs[seg0].leader];
         if (!L.active || L.mode != 0) return;
         ident1 = L.iters == 0;
@@ -797,10 +861,12 @@ __global__ void __launch_bounds__(THREADS, 1536 / THREADS) k2_spmv(Ctx* __restri
         int64_t ncol = ncol1;
         if (!one_seg) {
             S = segs + tile_seg[t];
-            const Seg& L = segs[S->leader];
-            if (!L.active || L.mode != 0) continue;
-            ident = L.iters == 0;
-            ncol = L.n;
+            if (!one_state) {
+                const Seg& L = segs[S->leader];
+                if (!L.active || L.mode != 0) continue;
+                ident = L.iters == 0;
+                ncol = L.n;
+            }
         }
         const RP* __restrict__ rp = (const RP*)S->rp;
         const int32_t* __restrict__ gf = S->gf;
@@ -1113,7 +1179,6 @@ __global__ void __launch_bounds__(FIRST_THREADS)
 // for each bound the number of first-iteration tiles whose entries all lie
 // below it (tiles end at non-decreasing entry positions, so each count is a
 // binary search): chunk c's launch of k2_first takes tiles [out[c], out[c+1]).
-constexpr int MAX_FEED_CHUNKS = 16;
 struct FeedBounds {
     int64_t b[MAX_FEED_CHUNKS + 1];  // b[c + 1]: entries copied once chunk c has landed
     int32_t chunks;

@@ -43,6 +43,17 @@ struct Seg {
                             // entries; bit 31 set: merge its minimum atomically); nullptr: identity
 };
 
+constexpr int MAX_COL_BLOCKS = 32;   // column blocks of one graph
+constexpr int MAX_FEED_CHUNKS = 16;  // chunks of the column-block copy (and of a host-fed col_idx)
+
+// where the blocks of one chunk of the column-block copy start in colB and
+// rowsB (computed on the device from the chunk's scanned totals; entry b + 1
+// is the end of block b)
+struct ChunkLayout {
+    int64_t ebase[MAX_COL_BLOCKS + 1];
+    int64_t pbase[MAX_COL_BLOCKS + 1];
+};
+
 // Ctx::mode bits: some active graph runs a full SpMV / pushes this iteration
 constexpr int32_t MODE_DENSE = 1;
 constexpr int32_t MODE_PUSH = 2;
@@ -87,6 +98,7 @@ struct Ctx {
     int32_t sparse_div;
     int32_t sparse_iters;          // iterations graph 0 ran in push mode in this call
     unsigned long long loop_kernels_total;  // device-loop kernel launches over all calls (never reset)
+    int32_t blk_chunks;            // segments per column block of graph 0 (one per chunk of its copy)
     Summary sum;
 };
 

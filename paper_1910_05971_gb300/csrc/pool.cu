@@ -115,6 +115,7 @@ __global__ void k_pool_begin(Ctx* ctx, int32_t loop_limit, int32_t* frontier, in
         ctx->k3_done = 0;
         ctx->sparse_enabled = sparse_div > 0 && frontier != nullptr;
         ctx->sparse_div = sparse_div;
+        ctx->blk_chunks = 1;
         ctx->frontier = frontier;
         ctx->frontier_cap = (unsigned int)(frontier_cap < 0x7fffffff ? frontier_cap : 0x7fffffff);
         ctx->mode = (s_dense ? MODE_DENSE : 0) | (s_push ? MODE_PUSH : 0);

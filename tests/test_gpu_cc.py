@@ -231,8 +231,10 @@ def test_host_buffer_entry_point():
 def test_host_buffer_entry_point_column_blocked(col_blocks):
     """fastsv_cc_host on a column-blocked solve copies col_idx in chunks that
     overlap the first iteration (each chunk's tiles run once their entries
-    have landed): labels, iterations and the per-iteration trace must still
-    be Algorithm 2's, on repeated calls into the same device buffers."""
+    have landed; from the second call on, each chunk is also split into the
+    column blocks right away): labels, iterations and the per-iteration trace
+    must still be Algorithm 2's, on repeated calls into the same device
+    buffers."""
     import paper_1910_05971_gb300 as fsv
     torch = pytest.importorskip("torch")
     for seed in (8, 9):
@@ -247,6 +249,24 @@ def test_host_buffer_entry_point_column_blocked(col_blocks):
                 assert st["col_blocks"] > 1
                 assert np.array_equal(lab.numpy(), f) and st["iterations"] == it
                 assert st["changed_per_iter"] == ch.tolist()
+
+
+def test_host_buffer_column_blocked_runs_outgrow_an_earlier_call():
+    """The chunk-by-chunk block copy of fastsv_cc_host sizes its run arrays
+    from the handle's earlier calls; a larger graph after a smaller one
+    overflows them, and the call must notice, grow them and copy again."""
+    import paper_1910_05971_gb300 as fsv
+    torch = pytest.importorskip("torch")
+    small = graphgen.rmat(11, 16, seed=3, permute=True)
+    large = graphgen.rmat(13, 16, seed=4, permute=True)
+    with fsv.FastSV(col_blocks=4) as s:
+        for rp, ci in (small, large, large, small):
+            f, it, _, ch = oracle.fastsv(rp, ci, form="omp")
+            lab = s.cc_host(torch.from_numpy(rp).pin_memory(), torch.from_numpy(ci).pin_memory())
+            st = s.stats()
+            assert st["col_blocks"] == 4
+            assert np.array_equal(lab.numpy(), f) and st["iterations"] == it
+            assert st["changed_per_iter"] == ch.tolist()
 
 
 def test_non_default_stream_and_launch_count():
@@ -280,10 +300,11 @@ def test_launch_count_over_unsynchronised_calls(col_blocks):
             assert one == 4 + 5 * it
         else:
             # set-up (3), the first iteration on the original CSR (4), the
-            # scan of its block counts and their totals (4), the block split
-            # and the blocks' set-up (4), finish (1); then 4 + col_blocks
-            # kernels per device-loop iteration
-            assert one == 16 + (4 + col_blocks) * (it - 1)
+            # scan of its block counts and the blocks' layout (4), the check
+            # of the copy's totals (1), the block split and the blocks'
+            # set-up (4), finish (1); then 4 + col_blocks kernels per
+            # device-loop iteration
+            assert one == 17 + (4 + col_blocks) * (it - 1)
         for _ in range(5):
             s.cc(rp_d, ci_d, lab, check_status=False)
         s.check_last()
