@@ -680,6 +680,28 @@ static fastsv_status launch_chunk_layout(fastsv_ctx* h, const BlockBuild& B, int
     return FASTSV_OK;
 }
 
+// The first iteration's hooks and grandparents, once its SpMV (every chunk
+// of it) is enqueued on s, on a stream of their own: they touch none of what
+// the block copy reads or writes, so they run beside it (build_blocks joins
+// them before the blocks become segments).
+static fastsv_status launch_first_hooks(fastsv_ctx* h, const IterKernels& K, cudaStream_t s) {
+    if (!h->side_stream) FSV_CUDA(h, cudaStreamCreateWithFlags(&h->side_stream, cudaStreamNonBlocking));
+    for (cudaEvent_t& ev : h->side_ev)
+        if (!ev) FSV_CUDA(h, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    Ctx* ctx = h->d_ctx;
+    cudaGraphConditionalHandle none = 0;
+    int no_cond = 0;
+    void* a_ctx[] = {(void*)&ctx};
+    void* a_k3[] = {(void*)&ctx, (void*)&none, (void*)&no_cond};
+    FSV_CUDA(h, cudaEventRecord(h->side_ev[0], s));
+    FSV_CUDA(h, cudaStreamWaitEvent(h->side_stream, h->side_ev[0], 0));
+    FSV_CUDA(h, cudaLaunchKernel(K.hook, dim3(K.vtx_grid), dim3(K3_THREADS), a_ctx, 0, h->side_stream));
+    FSV_CUDA(h, cudaLaunchKernel(K.k3, dim3(K.vtx_grid), dim3(K3_THREADS), a_k3, 0, h->side_stream));
+    FSV_CUDA(h, cudaEventRecord(h->side_ev[1], h->side_stream));
+    h->pending_fixed_launches += 2;
+    return FASTSV_OK;
+}
+
 // one iteration on segment 0's own tiles (BUILD_TILE items each), launched
 // kernel by kernel: the first iteration of a column-blocked solve.  Its SpMV
 // (k2_first) gathers nothing, so the per-tile merge-path search is most of
@@ -707,8 +729,6 @@ static fastsv_status first_iteration_unblocked(fastsv_ctx* h, const BlockBuild& 
     cudaGraphConditionalHandle none = 0;
     int no_cond = 0;
     void* a_begin[] = {(void*)&ctx, (void*)&none, (void*)&no_cond};
-    void* a_ctx[] = {(void*)&ctx};
-    void* a_k3[] = {(void*)&ctx, (void*)&none, (void*)&no_cond};
     FSV_CUDA(h, cudaLaunchKernel((const void*)k_iter_begin, dim3(K.vtx_grid), dim3(256), a_begin, 0, s));
     h->pending_fixed_launches += 1;
     if (!feed) {
@@ -717,6 +737,7 @@ static fastsv_status first_iteration_unblocked(fastsv_ctx* h, const BlockBuild& 
         void* a_spmv[] = {(void*)&ctx, (void*)&cnt, (void*)&nb, (void*)&shift, (void*)&range, (void*)&chunk};
         FSV_CUDA(h, cudaLaunchKernel(spmv, dim3(grid), dim3(FIRST_THREADS), a_spmv, smem, s));
         h->pending_fixed_launches += 1;
+        if ((st = launch_first_hooks(h, K, s)) != FASTSV_OK) return st;
     } else {
         // col_idx arrives in FEED_CHUNKS copies on the feed stream (after
         // everything enqueued on s so far); every chunk's tiles run as soon as
@@ -742,6 +763,7 @@ static fastsv_status first_iteration_unblocked(fastsv_ctx* h, const BlockBuild& 
             int chunk = c;
             void* a_spmv[] = {(void*)&ctx, (void*)&cnt, (void*)&nb, (void*)&shift, (void*)&range, (void*)&chunk};
             FSV_CUDA(h, cudaLaunchKernel(spmv, dim3(grid), dim3(FIRST_THREADS), a_spmv, smem, s));
+            if (c == FEED_CHUNKS - 1 && (st = launch_first_hooks(h, K, s)) != FASTSV_OK) return st;
             if (pipelined) {
                 if ((st = launch_chunk_layout(h, B, c, s)) != FASTSV_OK) return st;
                 if ((st = launch_chunk_split<RP>(h, B, c, s)) != FASTSV_OK) return st;
@@ -749,9 +771,6 @@ static fastsv_status first_iteration_unblocked(fastsv_ctx* h, const BlockBuild& 
         }
         h->pending_fixed_launches += 1 + FEED_CHUNKS;
     }
-    FSV_CUDA(h, cudaLaunchKernel(K.hook, dim3(K.vtx_grid), dim3(K3_THREADS), a_ctx, 0, s));
-    FSV_CUDA(h, cudaLaunchKernel(K.k3, dim3(K.vtx_grid), dim3(K3_THREADS), a_k3, 0, s));
-    h->pending_fixed_launches += 2;
     return FASTSV_OK;
 }
 
@@ -777,7 +796,10 @@ static fastsv_status build_blocks(fastsv_ctx* h, const BlockBuild& B, bool pipel
     FSV_CUDA(h, cudaMemcpyAsync(h->h_scalar, h->d_build_scalars, 3 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     FSV_CUDA(h, cudaStreamSynchronize(s));
     const int64_t ends = h->h_scalar[0], runs = h->h_scalar[1], contiguous = h->h_scalar[2];
-    if (ends != B.m || !contiguous) return FASTSV_ERR_INVALID_GRAPH;  // row_ptr not a valid CSR of m entries
+    if (ends != B.m || !contiguous) {  // row_ptr not a valid CSR of m entries
+        FSV_CUDA(h, cudaStreamWaitEvent(s, h->side_ev[1], 0));  // later work on s follows the hooks
+        return FASTSV_ERR_INVALID_GRAPH;
+    }
     const int64_t slots = (int64_t)B.nb * C;
     const bool fits = pipelined && runs + slots <= h->cap_runs;
     if ((st = ensure_run_workspace(h, runs, slots)) != FASTSV_OK) return st;
@@ -787,6 +809,7 @@ static fastsv_status build_blocks(fastsv_ctx* h, const BlockBuild& B, bool pipel
         for (int c = 0; c < C; ++c)
             if ((st = launch_chunk_split<RP>(h, pipelined ? B : one, c, s)) != FASTSV_OK) return st;
     }
+    FSV_CUDA(h, cudaStreamWaitEvent(s, h->side_ev[1], 0));  // the first iteration's hooks are done
     k_setup_blocks<<<1, 256, 0, s>>>(h->d_ctx, h->d_clay, C, B.nb, h->d_colB, h->d_rowsB, h->d_endsB, tile);
     k_scan_tiles<<<1, 1024, 0, s>>>(h->d_ctx);
     k_partition<int32_t><<<setup_grid(h), 256, 0, s>>>(h->d_ctx);
@@ -1019,6 +1042,9 @@ fastsv_status fastsv_destroy(fastsv_t h) {
     dev_free((void**)&h->d_ctot);
     dev_free((void**)&h->d_feed_tiles);
     if (h->feed_stream) cudaStreamDestroy(h->feed_stream);
+    if (h->side_stream) cudaStreamDestroy(h->side_stream);
+    for (cudaEvent_t& ev : h->side_ev)
+        if (ev) cudaEventDestroy(ev);
     for (cudaEvent_t& ev : h->feed_ev)
         if (ev) cudaEventDestroy(ev);
     dev_free(&h->d_rp_copy);

@@ -87,6 +87,9 @@ struct fastsv_ctx {
     // first iteration of a column-blocked solve
     cudaStream_t feed_stream = nullptr;
     cudaEvent_t feed_ev[17] = {};        // [0]: the call's stream reached the copies; [1 + c]: chunk c landed
+    // a column-blocked graph's first hooks run beside its block copy
+    cudaStream_t side_stream = nullptr;
+    cudaEvent_t side_ev[2] = {};         // [0]: the first iteration's SpMV is done; [1]: its hooks are
     int64_t* d_feed_tiles = nullptr;     // first-iteration tile range of every chunk
 
     // device copies for the host-buffer entry point
