@@ -1252,6 +1252,10 @@ __global__ void __launch_bounds__(256) k2_push(Ctx* __restrict__ ctx) {
 //                        gf[u], because f[p[u]] <= p[p[u]] = gf[u] throughout)
 //   aggressive hooking  f_next[u] <-min mngf[u]
 //   shortcutting        f_next[u] <-min gf[u]
+// Many vertices hook to the same root (the hot spot of Section 4.2): a
+// stochastic hook first reads the root's current value and issues its atomic
+// only when it would lower it.  f only decreases, so a skipped atomic could
+// not have changed it, and the result is the same minimum.
 __global__ void __launch_bounds__(K3_THREADS) k2_hook(Ctx* __restrict__ ctx) {
     const int64_t T = ctx->k3_total;
     const int tid = threadIdx.x;
@@ -1281,7 +1285,7 @@ __global__ void __launch_bounds__(K3_THREADS) k2_hook(Ctx* __restrict__ ctx) {
         for (int q = 0; q < K3_ITEMS; ++q) {
             if (mn[q] == INF) continue;
             const int64_t v = v0 + tid + q * K3_THREADS;
-            if (mn[q] < g[q]) atomicMin(f + pu[q], mn[q]);
+            if (mn[q] < g[q] && mn[q] < __ldcg(f + pu[q])) atomicMin(f + pu[q], mn[q]);
             const int32_t m2 = mn[q] < g[q] ? mn[q] : g[q];
             if (m2 < pu[q]) atomicMin(f + v, m2);
         }
