@@ -1005,10 +1005,10 @@ constexpr int k2_smem_bytes() {
 // mngf[u] is u's smallest neighbour id and nothing is gathered.  The same
 // walk counts, per tile and column block, the tile's entries and runs (see
 // the block copy's layout) into cnt[b][t] and cnt[nb + b][t] (rows of
-// tiles + 1 entries; the last entry of each row is 0, so that an exclusive
-// scan of the row ends in the row's total): every thread follows its items'
-// segments of one row and one block and adds each segment to the tile's
-// counters when it ends.
+// tiles + 1 entries, the last one 0; a chunk's exclusive scan over its tiles
+// turns them into offsets, and its sum is the chunk's total): every thread
+// follows its items' segments of one row and one block and adds each
+// segment to the tile's counters when it ends.
 constexpr int FIRST_THREADS = 64;
 constexpr int FIRST_ITEMS = 16;
 static_assert(FIRST_THREADS * FIRST_ITEMS == BUILD_TILE, "the block copy cuts along the first iteration's tiles");
