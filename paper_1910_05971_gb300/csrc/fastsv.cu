@@ -795,19 +795,22 @@ static fastsv_status build_blocks(fastsv_ctx* h, const BlockBuild& B, bool pipel
     FSV_CUDA(h, cudaGetLastError());
     FSV_CUDA(h, cudaMemcpyAsync(h->h_scalar, h->d_build_scalars, 3 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     FSV_CUDA(h, cudaStreamSynchronize(s));
+    // an error return leaves s (and so every later call) after the first
+    // iteration's hooks on the side stream
+    auto fail = [&](fastsv_status e) {
+        cudaStreamWaitEvent(s, h->side_ev[1], 0);
+        return e;
+    };
     const int64_t ends = h->h_scalar[0], runs = h->h_scalar[1], contiguous = h->h_scalar[2];
-    if (ends != B.m || !contiguous) {  // row_ptr not a valid CSR of m entries
-        FSV_CUDA(h, cudaStreamWaitEvent(s, h->side_ev[1], 0));  // later work on s follows the hooks
-        return FASTSV_ERR_INVALID_GRAPH;
-    }
+    if (ends != B.m || !contiguous) return fail(FASTSV_ERR_INVALID_GRAPH);  // row_ptr not a valid CSR of m entries
     const int64_t slots = (int64_t)B.nb * C;
     const bool fits = pipelined && runs + slots <= h->cap_runs;
-    if ((st = ensure_run_workspace(h, runs, slots)) != FASTSV_OK) return st;
+    if ((st = ensure_run_workspace(h, runs, slots)) != FASTSV_OK) return fail(st);
     h->last_runs = runs;
     if (!fits) {
         // split now (one chunk), or again with room for every run
         for (int c = 0; c < C; ++c)
-            if ((st = launch_chunk_split<RP>(h, pipelined ? B : one, c, s)) != FASTSV_OK) return st;
+            if ((st = launch_chunk_split<RP>(h, pipelined ? B : one, c, s)) != FASTSV_OK) return fail(st);
     }
     FSV_CUDA(h, cudaStreamWaitEvent(s, h->side_ev[1], 0));  // the first iteration's hooks are done
     k_setup_blocks<<<1, 256, 0, s>>>(h->d_ctx, h->d_clay, C, B.nb, h->d_colB, h->d_rowsB, h->d_endsB, tile);
